@@ -1,0 +1,88 @@
+"""The oracle's pins must catch plausible mistakes.  Each case copies the
+oracle source to a temporary directory, plants ONE mistake (a dropped term, a
+wrong sign, a wrong index or comparison), compiles it there, and checks that
+the hand-worked examples or the brute-force cross-check reject it.  Nothing is
+planted in the real oracle."""
+import ctypes
+import itertools
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from golden_format import cases, side_rows, trade_rows
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "lob_oracle.cpp")
+
+MUTANTS = {
+    "fill_sign": ("std::max(0, Q_s - Q_a)", "std::max(0, Q_a - Q_s)"),
+    "trade_qty_term": ("t.qty = Q_s - Q_s_new;", "t.qty = Q_s;"),
+    "trade_price_from_aggressor": ("t.price = s.price;", "t.price = P_a;"),
+    "cross_strict": ("(P_a <= s.price) : (P_a >= s.price)", "(P_a < s.price) : (P_a > s.price)"),
+    "bid_best_is_min": ("return is_bid ? levels.rbegin()->second : levels.begin()->second;",
+                        "return levels.begin()->second;"),
+    "cancel_keeps_zero": ("if (q_new <= 0) {  // Q <= 0", "if (q_new < 0) {  // Q <= 0"),
+    "lifo_in_level": ("Order& best() { return best_level().front(); }",
+                      "Order& best() { return best_level().back(); }"),
+    "evict_on_equal": ("own.strictly_better(m.price, own.worst().price)",
+                       "!own.strictly_better(own.worst().price, m.price)"),
+    "market_rests": ("bk.counters[C_MARKET_DISCARDED_QTY] += rest;",
+                     "bk.counters[C_MARKET_DISCARDED_QTY] += rest; if (rest > 0) add(E, bk, m, rest);"),
+}
+
+
+def _build_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, name
+    path = tmp_path / ("%s.cpp" % name)
+    path.write_text(src.replace(old, new))
+    so = tmp_path / ("lib%s.so" % name)
+    subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-pthread", "-o", str(so),
+                    str(path)], check=True, capture_output=True)
+    return str(so)
+
+
+def _golden_ok(lib):
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.oracle_create.restype = vp
+    lib.oracle_create.argtypes = [i32] * 5
+    lib.oracle_process.restype = ctypes.c_int64
+    lib.oracle_process.argtypes = [vp, vp, vp, vp, i32, i32]
+    lib.oracle_get_book.argtypes = [vp] * 7
+    lib.oracle_get_trades.argtypes = [vp] * 3
+    lib.oracle_destroy.argtypes = [vp]
+    for c in cases():
+        h = lib.oracle_create(1, c.capacity, c.trade_capacity, c.rule, 0)
+        m = c.message_array()
+        off = np.array([0, len(m)], np.int64)
+        lib.oracle_process(h, vp(m.ctypes.data), vp(off.ctypes.data), None, 1, 1)
+        shp = (1, 2, c.capacity)
+        px, qty, oid, tid = (np.empty(shp, np.int32) for _ in range(4))
+        tm = np.empty(shp, np.int64)
+        cnt = np.empty((1, 2), np.int32)
+        lib.oracle_get_book(h, *[vp(a.ctypes.data) for a in (px, qty, oid, tid, tm, cnt)])
+        tr = np.empty((1, c.trade_capacity), oracle.TRADE_DTYPE)
+        tc = np.empty(1, np.int64)
+        lib.oracle_get_trades(h, vp(tr.ctypes.data), vp(tc.ctypes.data))
+        lib.oracle_destroy(h)
+        bk = dict(price=px, qty=qty, oid=oid, tid=tid, time_ns=tm, count=cnt)
+        if (side_rows(bk, 0, 0) != c.bids or side_rows(bk, 0, 1) != c.asks
+                or trade_rows(tr, tc, 0, c.trade_capacity) != c.trades
+                or int(tc[0]) != c.trades_total):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_golden_examples_reject_mutant(tmp_path, name):
+    old, new = MUTANTS[name]
+    lib = ctypes.CDLL(_build_mutant(tmp_path, name, old, new))
+    assert not _golden_ok(lib), "planted mistake %r went unnoticed" % name
+
+
+def test_unmutated_copy_passes(tmp_path):
+    lib = ctypes.CDLL(_build_mutant(tmp_path, "identity", "int oracle_abi_version(void) { return 1; }",
+                                    "int oracle_abi_version(void) { return 1; }"))
+    assert _golden_ok(lib)
