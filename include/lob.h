@@ -1,0 +1,236 @@
+/*
+ * lob.h -- C ABI of the batched limit-order-book engine (liblob.so).
+ *
+ * Thousands of independent limit order books, each with a fixed capacity of N
+ * orders per side, process their own message streams in parallel on one GPU
+ * (the batching over books of Sec. 4.3).  Within a book messages are applied
+ * strictly in order with price-time priority (Sec. 4.1-4.2).
+ *
+ * Conventions for every entry point below:
+ *   - Pointers named d_* are DEVICE pointers owned by the caller (for example
+ *     torch CUDA tensors); the library never frees them and keeps no reference
+ *     to them after the call returns.  The library owns only what lob_create /
+ *     lob_env_create allocate (book state, trade log, counters, work queue).
+ *   - Every call is asynchronous and ordered on `stream` (a cudaStream_t; NULL
+ *     means the legacy default stream).  Results are ready once the stream has
+ *     reached the call.
+ *   - Return value: LOB_OK (0) or a negative LOB_E_* code; nothing is thrown
+ *     across the ABI.  Argument errors are detected on the host before any
+ *     launch and leave the context untouched.  lob_last_error() describes the
+ *     most recent failure of the calling thread.
+ *   - Anomalies found on the device (a book id out of range, a message chunk
+ *     that did not arrive in time) never fault: the affected work item is
+ *     skipped and a LOB_STATUS_* bit is OR-ed into the context's status word
+ *     (lob_get_stats).
+ *   - A context must be used from one stream at a time and with the device it
+ *     was created on current.
+ */
+#ifndef LOB_H
+#define LOB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- records */
+
+/* Message m = [T, S, Q, P, OID, TID, Ts, Tns] (Sec. 4.2, eq. message), with the
+ * two 32-bit time fields joined into one int64 nanosecond stamp.  32 bytes.
+ *   type : 0 padding (never processed, cf. the zero-padded steps of Sec. 5.1.1)
+ *          1 limit order, 2 cancel, 3 delete, 4 market order
+ *   side : +1 bid (buy), -1 ask (sell)
+ *   price: integer ticks; ignored for cancels, deletes and market orders
+ *   qty  : order size, or the quantity to remove for a cancel/delete
+ *   oid  : order id; a cancel/delete names the order it removes from
+ *   tid  : trader id, copied into trade records
+ *   time_ns: copied into the resting order and into trades it aggresses.
+ * Priority between resting orders is arrival order within the book; the time
+ * stamp is never compared.  Malformed messages (type outside 0..4, side not
+ * +-1, qty <= 0, limit price <= 0) are skipped and counted (LOB_CTR_INVALID).
+ * A limit order whose id is already live on its side is a contract violation
+ * (behaviour unspecified). */
+typedef struct {
+    int32_t type, side, price, qty, oid, tid;
+    int64_t time_ns;
+} lob_msg_t;
+
+/* Trade t = [P_j, Q_j, OID_a, OID_s, Ts, Tns] (Sec. 4.1, eq. trade) plus the
+ * two trader ids: price = the standing order's price, qty = the filled
+ * quantity, time_ns = the aggressor's time.  32 bytes. */
+typedef struct {
+    int32_t price, qty, oid_aggr, oid_stand, tid_aggr, tid_stand;
+    int64_t time_ns;
+} lob_trade_t;
+
+/* ------------------------------------------------------------ configuration */
+
+enum {
+    LOB_OVERFLOW_EVICT = 0,  /* full side: evict the worst resting order when the
+                                incoming rest has a strictly better price, else
+                                reject the rest                                  */
+    LOB_OVERFLOW_REJECT = 1  /* full side: always reject the rest               */
+};
+
+enum {
+    LOB_FLAG_APPEND_TRADES = 1  /* the trade log of a book keeps growing across
+                                   lob_process_batch calls until lob_clear_trades
+                                   (default: each call restarts the log of the
+                                   books it touches)                            */
+};
+
+typedef struct {
+    int32_t n_books;         /* independent books, >= 1                           */
+    int32_t capacity;        /* N: orders per side, 1..512 (Sec. 4)               */
+    int32_t trade_capacity;  /* trades stored per book per call, >= 0; further
+                                trades still execute and are counted (eq. trades) */
+    int32_t overflow_rule;   /* LOB_OVERFLOW_*                                     */
+    int32_t flags;           /* LOB_FLAG_*                                         */
+} lob_config_t;
+
+enum {
+    LOB_OK = 0,
+    LOB_E_INVAL = -1,    /* bad argument (null pointer, size, alignment, range) */
+    LOB_E_NOMEM = -2,    /* device or host allocation failed                     */
+    LOB_E_CUDA = -3,     /* a CUDA runtime call failed                           */
+    LOB_E_TIMEOUT = -4,  /* a bounded device wait gave up (see status word)      */
+    LOB_E_STATE = -5     /* call not valid in the context's current state        */
+};
+
+/* status word bits (device-side anomalies, sticky until lob_reset) */
+enum {
+    LOB_STATUS_TIMEOUT = 1,       /* a message chunk did not arrive within the wait bound */
+    LOB_STATUS_BAD_BOOK = 2,      /* a book id outside [0, n_books) was skipped            */
+    LOB_STATUS_BAD_SEGMENT = 4,   /* a segment with offsets[i+1] < offsets[i] was skipped  */
+    LOB_STATUS_BAD_BOOK_LOAD = 8  /* lob_set_book: a side not in priority order was emptied */
+};
+
+/* per-book counters (int64), in this order */
+enum {
+    LOB_CTR_MSGS = 0,          /* messages examined (padding and invalid included) */
+    LOB_CTR_LIMIT,             /* valid limit orders                               */
+    LOB_CTR_CANCEL,            /* valid cancels + deletes                          */
+    LOB_CTR_MARKET,            /* valid market orders                              */
+    LOB_CTR_NOOP,              /* type-0 padding                                   */
+    LOB_CTR_INVALID,           /* malformed messages skipped                       */
+    LOB_CTR_TRADES,            /* trades executed                                  */
+    LOB_CTR_TRADED_QTY,        /* sum of trade quantities                          */
+    LOB_CTR_RESTED,            /* limit remainders placed on the book              */
+    LOB_CTR_REJECTED,          /* remainders rejected by the full-side rule        */
+    LOB_CTR_REJECTED_QTY,
+    LOB_CTR_EVICTED,           /* resting orders evicted by the full-side rule     */
+    LOB_CTR_EVICTED_QTY,
+    LOB_CTR_CANCEL_HIT,        /* cancels/deletes that found their order           */
+    LOB_CTR_CANCELLED_QTY,
+    LOB_CTR_CANCEL_MISS,       /* cancels/deletes whose id is not live on that side */
+    LOB_CTR_MARKET_DISCARDED_QTY, /* unmatched market quantity (dropped)           */
+    LOB_CTR_LIMIT_QTY,         /* quantity submitted by valid limit orders         */
+    LOB_CTR_MARKET_QTY,        /* quantity submitted by valid market orders        */
+    LOB_CTR_TRADES_DROPPED,    /* trades executed but not stored (log full)        */
+    LOB_N_COUNTERS
+};
+
+typedef struct lob_ctx lob_ctx;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Create a context with `cfg->n_books` empty books (all sides empty, counters
+ * zero).  Allocates the book state (48 * roundup(capacity, 32) bytes per
+ * book), the trade log (32 * trade_capacity bytes per book) and counters on
+ * the current device, and zeroes them on `stream`.  *out is set only on
+ * success.  Errors: LOB_E_INVAL (bad config), LOB_E_NOMEM, LOB_E_CUDA. */
+int lob_create(lob_ctx** out, const lob_config_t* cfg, void* stream);
+
+/* Release everything the context owns (synchronises its device first).
+ * NULL is accepted.  Returns LOB_OK or LOB_E_CUDA. */
+int lob_destroy(lob_ctx* ctx);
+
+/* Empty every book, clear the trade logs, counters and status word. */
+int lob_reset(lob_ctx* ctx, void* stream);
+
+/* -------------------------------------------------------------- processing */
+
+/* Apply message segments to books (Sec. 4.2 dispatch; Sec. 4.1 add, cancel,
+ * match; Sec. 4.3 batching over independent books).
+ *   d_msgs     : messages, 16-byte aligned, segment i = d_msgs[d_offsets[i] ..
+ *                d_offsets[i+1]) in arrival order
+ *   d_offsets  : int64[n_active + 1], non-decreasing
+ *   d_book_ids : int32[n_active] target book of each segment, pairwise
+ *                distinct; NULL means segment i -> book i (then n_active must
+ *                equal n_books)
+ *   n_active   : number of segments, 0..n_books (0 is a no-op)
+ * Each touched book's trade log restarts (unless LOB_FLAG_APPEND_TRADES) and
+ * receives the trades of its segment in execution order.  Books run as
+ * independent work items pulled from a device work queue by a persistent
+ * grid (one warp per book, book state staged in shared memory, message chunks
+ * fetched by bulk asynchronous copies). */
+int lob_process_batch(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                      const int32_t* d_book_ids, int32_t n_active, void* stream);
+
+/* Same as lob_process_batch, but the trades are appended to the log of the
+ * previous call (for orders injected after a replay, Sec. 5.1.3 step 4). */
+int lob_inject_orders(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                      const int32_t* d_book_ids, int32_t n_active, void* stream);
+
+/* Restart every book's trade log (count 0). */
+int lob_clear_trades(lob_ctx* ctx, void* stream);
+
+/* ----------------------------------------------------------------- outputs */
+
+/* Top `depth` price levels per side (Sec. 5.1.1 ten-level book state): for the
+ * k-th best distinct price, the price and the summed quantity of its orders
+ * (saturating at INT32_MAX); missing levels are (-1, 0).  Each output is
+ * int32[n_books][depth].  depth 1..64. */
+int lob_get_levels(lob_ctx* ctx, int32_t depth, int32_t* d_bid_px, int32_t* d_bid_qty,
+                   int32_t* d_ask_px, int32_t* d_ask_qty, void* stream);
+
+/* Trade logs: d_out is lob_trade_t[n_books][trade_capacity] in execution
+ * order, entries past the stored count all -1; d_counts int64[n_books] is the
+ * number of trades executed (may exceed trade_capacity).  Either pointer may
+ * be NULL to skip it. */
+int lob_get_trades(lob_ctx* ctx, lob_trade_t* d_out, int64_t* d_counts, void* stream);
+
+/* Canonical book dump: per field [n_books][2][capacity] (side 0 bids, side 1
+ * asks), orders in priority order (best price first, then arrival), unused
+ * slots -1; d_count int32[n_books][2].  Any pointer may be NULL. */
+int lob_get_book(lob_ctx* ctx, int32_t* d_price, int32_t* d_qty, int32_t* d_oid,
+                 int32_t* d_tid, int64_t* d_time, int32_t* d_count, void* stream);
+
+/* Load books from the canonical layout above (checkpoint restore, or a book
+ * initialised from a level snapshot).  Each side must be in priority order
+ * with 0 <= count <= capacity and positive prices and quantities; a side that
+ * is not is loaded empty and LOB_STATUS_BAD_BOOK_LOAD is set.  Trade logs,
+ * counters and the status word are left as they are. */
+int lob_set_book(lob_ctx* ctx, const int32_t* d_price, const int32_t* d_qty,
+                 const int32_t* d_oid, const int32_t* d_tid, const int64_t* d_time,
+                 const int32_t* d_count, void* stream);
+
+/* Counters int64[n_books][LOB_N_COUNTERS] (cumulative since create/reset) and
+ * the status word (int32, LOB_STATUS_* bits).  Either pointer may be NULL. */
+int lob_get_stats(lob_ctx* ctx, int64_t* d_counters, int32_t* d_status, void* stream);
+
+/* ------------------------------------------------------------------ tuning */
+
+/* Launch shape of the processing kernel: warps (= books in flight) per CTA
+ * (1..16; 1..8 for capacity > 128), messages per staged chunk (8..1024,
+ * multiple of 8), and CTAs per SM for the persistent grid (0 = as many as
+ * fit).  Takes effect for later calls.  Returns LOB_E_INVAL when the shape
+ * does not fit in shared memory. */
+int lob_set_launch(lob_ctx* ctx, int32_t warps_per_cta, int32_t chunk_msgs,
+                   int32_t ctas_per_sm);
+
+/* Number of kernel launches this context has issued since creation. */
+int64_t lob_launch_count(const lob_ctx* ctx);
+
+/* Human-readable description of the calling thread's most recent error. */
+const char* lob_last_error(void);
+
+/* Library ABI version (incremented on incompatible change). */
+int lob_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LOB_H */

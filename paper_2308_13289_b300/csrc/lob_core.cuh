@@ -1,0 +1,579 @@
+// lob_core.cuh -- warp-level order-book operations for sm_103a.
+//
+// One warp owns one book.  Each side of the book (Sec. 4, eqs. 1-2: arrays of
+// N orders [P, Q, OID, TID, time]) is held in shared memory SORTED BY PRIORITY:
+// slot 0 is Best(o) of eq. best_price (highest bid / lowest ask) and orders of
+// equal price sit in arrival order.  The paper keeps its arrays unsorted because
+// vmap turns every branch into a select and re-sorting would run on every message
+// (Sec. 4.3); a warp takes only the branch a message needs, so here the sorted
+// form is cheaper: the best order is slot 0, an insert or delete moves the tail
+// by one slot, and a multi-level match is one prefix scan instead of a loop.
+//
+// Blocked layout: capacity rounded up to C = 32*K slots, lane l holds slots
+// [l*K, l*K + K) of every field, so a lane reads its slots with 128-bit shared
+// loads and the warp never needs a barrier to move data between lanes (a
+// one-slot shift passes a single value per field through a shuffle).
+//
+// Field arrays of one side, in bytes from the side's base:
+//   px[C] int32 | qty[C] int32 | oid[C] int32 | tid[C] int32 | tm[C] int64
+// A book is [bid side][ask side] = 48*C bytes, the same layout in HBM and in
+// shared memory, so staging a book is one contiguous bulk copy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lob {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxK = 16;        // capacity <= 512
+constexpr int kNumCtr = 20;      // per-book counters (order fixed by the C ABI)
+constexpr int32_t kMaxInt = 2147483647;
+
+enum : int {
+    CTR_MSGS = 0, CTR_LIMIT, CTR_CANCEL, CTR_MARKET, CTR_NOOP, CTR_INVALID, CTR_TRADES,
+    CTR_TRADED_QTY, CTR_RESTED, CTR_REJECTED, CTR_REJECTED_QTY, CTR_EVICTED, CTR_EVICTED_QTY,
+    CTR_CANCEL_HIT, CTR_CANCELLED_QTY, CTR_CANCEL_MISS, CTR_MARKET_DISCARDED_QTY, CTR_LIMIT_QTY,
+    CTR_MARKET_QTY, CTR_TRADES_DROPPED
+};
+
+struct Msg {  // 32-byte message record {type, side, price, qty, oid, tid, time_ns}
+    int32_t type, side, price, qty, oid, tid;
+    int64_t time_ns;
+};
+struct Trade {  // 32-byte trade record
+    int32_t price, qty, oid_aggr, oid_stand, tid_aggr, tid_stand;
+    int64_t time_ns;
+};
+static_assert(sizeof(Msg) == 32 && sizeof(Trade) == 32, "record sizes");
+
+template <int K>
+struct Geo {
+    static constexpr int C = 32 * K;
+    static constexpr int PX = 0, QTY = 4 * C, OID = 8 * C, TID = 12 * C, TM = 16 * C;
+    static constexpr int SIDE_BYTES = 24 * C;
+    static constexpr int BOOK_BYTES = 2 * SIDE_BYTES;
+};
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// order this thread's earlier generic-proxy shared accesses before later
+// async-proxy (bulk copy) accesses
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 1-D bulk copy global -> shared, completion signalled on `bar` (bytes % 16 == 0,
+// both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of `bar`, giving up after `limit_ns` of wall time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// ------------------------------------------------------- lane-vector helpers
+
+template <int K>
+__device__ __forceinline__ void ld_vec(const int32_t* arr, int32_t (&v)[K])
+{
+    const int l = lane_id();
+    if constexpr (K == 1) {
+        v[0] = arr[l];
+    } else if constexpr (K == 2) {
+        int2 t = reinterpret_cast<const int2*>(arr)[l];
+        v[0] = t.x; v[1] = t.y;
+    } else {
+        const int4* q = reinterpret_cast<const int4*>(arr) + l * (K / 4);
+#pragma unroll
+        for (int i = 0; i < K / 4; ++i) {
+            int4 t = q[i];
+            v[4 * i] = t.x; v[4 * i + 1] = t.y; v[4 * i + 2] = t.z; v[4 * i + 3] = t.w;
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void st_vec(int32_t* arr, const int32_t (&v)[K])
+{
+    const int l = lane_id();
+    if constexpr (K == 1) {
+        arr[l] = v[0];
+    } else if constexpr (K == 2) {
+        reinterpret_cast<int2*>(arr)[l] = make_int2(v[0], v[1]);
+    } else {
+        int4* q = reinterpret_cast<int4*>(arr) + l * (K / 4);
+#pragma unroll
+        for (int i = 0; i < K / 4; ++i)
+            q[i] = make_int4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void ld_vec(const int64_t* arr, int64_t (&v)[K])
+{
+    const int l = lane_id();
+    if constexpr (K == 1) {
+        v[0] = arr[l];
+    } else {
+        const longlong2* q = reinterpret_cast<const longlong2*>(arr) + l * (K / 2);
+#pragma unroll
+        for (int i = 0; i < K / 2; ++i) {
+            longlong2 t = q[i];
+            v[2 * i] = t.x; v[2 * i + 1] = t.y;
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void st_vec(int64_t* arr, const int64_t (&v)[K])
+{
+    const int l = lane_id();
+    if constexpr (K == 1) {
+        arr[l] = v[0];
+    } else {
+        longlong2* q = reinterpret_cast<longlong2*>(arr) + l * (K / 2);
+#pragma unroll
+        for (int i = 0; i < K / 2; ++i) q[i] = make_longlong2(v[2 * i], v[2 * i + 1]);
+    }
+}
+
+// min(a + b, INT32_MAX) for a, b in [0, INT32_MAX] (no wrap: a + b < 2^32)
+__device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
+{
+    return min(a + b, (uint32_t)kMaxInt);
+}
+
+// ------------------------------------------------------------- one-side views
+
+// Side X: 0 = bids (priority = higher price first), 1 = asks (lower first).
+template <int K, int X>
+struct SideRef {
+    char* base;  // start of this side in shared memory
+    __device__ __forceinline__ int32_t* px() const { return reinterpret_cast<int32_t*>(base + Geo<K>::PX); }
+    __device__ __forceinline__ int32_t* qty() const { return reinterpret_cast<int32_t*>(base + Geo<K>::QTY); }
+    __device__ __forceinline__ int32_t* oid() const { return reinterpret_cast<int32_t*>(base + Geo<K>::OID); }
+    __device__ __forceinline__ int32_t* tid() const { return reinterpret_cast<int32_t*>(base + Geo<K>::TID); }
+    __device__ __forceinline__ int64_t* tm() const { return reinterpret_cast<int64_t*>(base + Geo<K>::TM); }
+    // a resting price `a` ranks at least as well as an incoming price `p`; on
+    // the opposite side of an aggressor this is exactly the crossing test
+    // (Sec. 4.1: buy crosses while P_a >= P_s, sell while P_a <= P_s)
+    static __device__ __forceinline__ bool at_least(int32_t a, int32_t p) { return X == 0 ? a >= p : a <= p; }
+};
+
+// Per-lane counter slot: lane i accumulates counter i of the current book.
+struct Counters {
+    int64_t v;
+    int lane;
+    __device__ __forceinline__ void add(int idx, int64_t x) { v += (lane == idx) ? x : 0; }
+};
+
+// ---------------------------------------------------------------- primitives
+
+// Shift slots [p, n_after) right by one and place `val` at slot p.
+template <int K, typename T>
+__device__ __forceinline__ void shift_in(T (&v)[K], int p, int n_after, T val)
+{
+    const int l = lane_id();
+    T prev = __shfl_up_sync(kFull, v[K - 1], 1);
+    T nv[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        T left = (j == 0) ? prev : v[j - 1];
+        nv[j] = (s == p) ? val : ((s > p && s < n_after) ? left : v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = nv[j];
+}
+
+// Shift slots [p+1, n) left by one (slot p disappears).
+template <int K, typename T>
+__device__ __forceinline__ void shift_out(T (&v)[K], int p, int n)
+{
+    const int l = lane_id();
+    T next = __shfl_down_sync(kFull, v[0], 1);
+    T nv[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        T right = (j == K - 1) ? next : v[j + 1];
+        nv[j] = (s >= p && s < n - 1) ? right : v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = nv[j];
+}
+
+// New slot s takes old slot s + m (0 < m): the first m slots disappear.
+// Slots at or past n - m are left undefined (they are beyond the new count).
+template <int K, typename T>
+__device__ __forceinline__ void drop_front(T (&v)[K], int m)
+{
+    const int l = lane_id();
+    const int a = m / K, b = m % K;  // K is a power of two
+    T r[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) r[j] = v[j];
+    // rotate lane-locally by b (warp-uniform): r[j] = v[(j + b) % K]
+#pragma unroll
+    for (int bit = 1; bit < K; bit <<= 1) {
+        if (b & bit) {
+            T t[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) t[j] = r[(j + bit) % K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) r[j] = t[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int src = (l + a + ((j + b) >= K ? 1 : 0)) & 31;
+        v[j] = __shfl_sync(kFull, r[j], src);
+    }
+}
+
+// Does this lane own a slot in [lo, hi)?
+template <int K>
+__device__ __forceinline__ bool lane_touches(int lo, int hi)
+{
+    const int s0 = lane_id() * K;
+    return s0 + K > lo && s0 < hi;
+}
+
+// Field-at-a-time versions (keep only one field's vector live).
+template <int K, typename T>
+__device__ __forceinline__ void field_shift_in(T* arr, int p, int n_after, T val, bool touch)
+{
+    T v[K];
+    ld_vec<K>(arr, v);
+    shift_in<K>(v, p, n_after, val);
+    if (touch) st_vec<K>(arr, v);
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void field_shift_out(T* arr, int p, int n, bool touch)
+{
+    T v[K];
+    ld_vec<K>(arr, v);
+    shift_out<K>(v, p, n);
+    if (touch) st_vec<K>(arr, v);
+}
+
+template <int K, typename T>
+__device__ __forceinline__ void field_drop_front(T* arr, T (&v)[K], int m, bool touch)
+{
+    drop_front<K>(v, m);
+    if (touch) st_vec<K>(arr, v);
+}
+
+// ------------------------------------------------------------ book operations
+
+// Add the remaining quantity Q as one new order (Sec. 4.1 item 1, Sec. 4.2
+// item 1) at the back of its price level on side X, with the full-side rule:
+// when the side already holds `cap` orders the worst one is evicted if the new
+// order's price is strictly better than its price, else the rest is rejected
+// (rule 1: always rejected).
+template <int K, int X>
+__device__ __forceinline__ void add_order(SideRef<K, X> sd, int& n, int cap, int rule, int32_t P,
+                                          int32_t Q, int32_t oid, int32_t tid, int64_t tm,
+                                          Counters& ctr)
+{
+    const int l = lane_id();
+    int32_t vpx[K];
+    ld_vec<K>(sd.px(), vpx);
+    // insertion point: number of resting orders with a price at least as good
+    unsigned cnt = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        cnt += (s < n && SideRef<K, X>::at_least(vpx[j], P)) ? 1u : 0u;
+    }
+    const int p = (int)__reduce_add_sync(kFull, cnt);
+    int n_after = n + 1;
+    if (n >= cap) {
+        if (rule != 0 || p >= cap) {
+            ctr.add(CTR_REJECTED, 1);
+            ctr.add(CTR_REJECTED_QTY, Q);
+            return;
+        }
+        // the worst order (slot cap-1) has a strictly worse price: evict it
+        const int32_t qe = sd.qty()[cap - 1];
+        ctr.add(CTR_EVICTED, 1);
+        ctr.add(CTR_EVICTED_QTY, qe);
+        n_after = cap;
+    }
+    const bool touch = lane_touches<K>(p, n_after);
+    shift_in<K>(vpx, p, n_after, P);
+    if (touch) st_vec<K>(sd.px(), vpx);
+    field_shift_in<K>(sd.qty(), p, n_after, Q, touch);
+    field_shift_in<K>(sd.oid(), p, n_after, oid, touch);
+    field_shift_in<K>(sd.tid(), p, n_after, tid, touch);
+    field_shift_in<K>(sd.tm(), p, n_after, tm, touch);
+    n = n_after;
+    ctr.add(CTR_RESTED, 1);
+}
+
+// Cancellation (Sec. 4.1 item 2): locate OID on side X and remove Q from it;
+// the order leaves the book when its quantity drops to 0 or below.
+template <int K, int X>
+__device__ __forceinline__ void cancel_order(SideRef<K, X> sd, int& n, int32_t oid, int32_t Q,
+                                             Counters& ctr)
+{
+    const int l = lane_id();
+    int32_t vo[K];
+    ld_vec<K>(sd.oid(), vo);
+    int jj = -1;
+#pragma unroll
+    for (int j = K - 1; j >= 0; --j)
+        if (l * K + j < n && vo[j] == oid) jj = j;
+    const unsigned hit = __ballot_sync(kFull, jj >= 0);
+    if (hit == 0) {
+        ctr.add(CTR_CANCEL_MISS, 1);
+        return;
+    }
+    ctr.add(CTR_CANCEL_HIT, 1);
+    const int L = __ffs(hit) - 1;
+    const int p = L * K + __shfl_sync(kFull, jj, L);
+    const int32_t q_old = sd.qty()[p];
+    const int32_t q_new = q_old - Q;
+    if (q_new > 0) {
+        if (l == L) sd.qty()[p] = q_new;
+        ctr.add(CTR_CANCELLED_QTY, Q);
+        return;
+    }
+    ctr.add(CTR_CANCELLED_QTY, q_old);
+    const bool touch = lane_touches<K>(p, n - 1);
+    shift_out<K>(vo, p, n);
+    if (touch) st_vec<K>(sd.oid(), vo);
+    field_shift_out<K>(sd.px(), p, n, touch);
+    field_shift_out<K>(sd.qty(), p, n, touch);
+    field_shift_out<K>(sd.tid(), p, n, touch);
+    field_shift_out<K>(sd.tm(), p, n, touch);
+    n -= 1;
+}
+
+// Where trades of the current book go and how many are already there.
+struct TradeSink {
+    Trade* log;      // this book's segment of the trade log
+    int64_t count;   // trades executed so far in this log (uniform)
+    int32_t cap;     // stored capacity
+};
+
+// Matching (Sec. 4.1 item 3 and its while loop) of an aggressor of quantity Q
+// with limit price P (0 / max_int for market orders, Sec. 4.2 item 3) against
+// opposite side Y.  The loop "take Best(o_s), apply Q_s' = max(0, Q_s - Q_a),
+// Q_a' = Q_a - Q_s, log t = [P_s, Q_s - Q_s', OID_a, OID_s, time_a]" visits the
+// crossing prefix of the priority-sorted side in order; the standing order at
+// slot s therefore receives min(Q_s, max(0, Q - (quantity of slots before s))),
+// which one saturating warp prefix scan gives for all slots at once.
+// Returns the aggressor's remaining quantity max(0, Q_a).
+template <int K, int Y>
+__device__ __forceinline__ int32_t match_order(SideRef<K, Y> sd, int& n, int32_t P, int32_t Q,
+                                               int32_t oid_a, int32_t tid_a, int64_t tm_a,
+                                               TradeSink& ts, Counters& ctr)
+{
+    const int l = lane_id();
+    int32_t vpx[K], vq[K];
+    ld_vec<K>(sd.px(), vpx);
+    ld_vec<K>(sd.qty(), vq);
+
+    // crossing quantity per slot and lane-local inclusive prefix
+    uint32_t cq[K], loc[K];
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        const bool c = s < n && SideRef<K, Y>::at_least(vpx[j], P);
+        cq[j] = c ? (uint32_t)vq[j] : 0u;
+        acc = sat_add(acc, cq[j]);
+        loc[j] = acc;
+    }
+    // warp inclusive scan of the lane totals (saturating at INT32_MAX: exact
+    // wherever the running total is below Q <= INT32_MAX, which is all that
+    // the fills depend on)
+    uint32_t incl = acc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if (l >= d) incl = sat_add(incl, t);
+    }
+    uint32_t excl = __shfl_up_sync(kFull, incl, 1);
+    if (l == 0) excl = 0;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+
+    int32_t fill[K];
+    unsigned nfull = 0, nfill = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const uint32_t before = sat_add(excl, j == 0 ? 0u : loc[j - 1]);
+        const uint32_t room = before < (uint32_t)Q ? (uint32_t)Q - before : 0u;
+        fill[j] = (int32_t)min(cq[j], room);
+        nfull += (cq[j] != 0u && (uint32_t)fill[j] == cq[j]) ? 1u : 0u;
+        nfill += fill[j] > 0 ? 1u : 0u;
+    }
+    const int m = (int)__reduce_add_sync(kFull, nfull);   // fully filled: leave the book
+    const int nf = (int)__reduce_add_sync(kFull, nfill);  // trades of this message
+    const int32_t F = (int32_t)min(total, (uint32_t)Q);    // quantity traded
+
+    // trades: the filled slots are the prefix [0, nf), trade k -> slot k
+    int32_t vo[K], vt[K];
+    ld_vec<K>(sd.oid(), vo);
+    ld_vec<K>(sd.tid(), vt);
+    const int32_t tlo = (int32_t)(uint32_t)(uint64_t)tm_a;
+    const int32_t thi = (int32_t)(uint32_t)((uint64_t)tm_a >> 32);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        const int64_t idx = ts.count + s;
+        if (fill[j] > 0 && idx < ts.cap) {
+            int4* dst = reinterpret_cast<int4*>(ts.log + idx);
+            dst[0] = make_int4(vpx[j], fill[j], oid_a, vo[j]);
+            dst[1] = make_int4(tid_a, vt[j], tlo, thi);
+        }
+    }
+    const int64_t stored_before = min(ts.count, (int64_t)ts.cap);
+    const int64_t stored_after = min(ts.count + nf, (int64_t)ts.cap);
+    ctr.add(CTR_TRADES_DROPPED, nf - (stored_after - stored_before));
+    ts.count += nf;
+    ctr.add(CTR_TRADES, nf);
+    ctr.add(CTR_TRADED_QTY, F);
+
+    // standing quantities after the fills (Q_s' per slot), then drop the m
+    // fully filled orders at the front (Q <= 0 cleanup)
+#pragma unroll
+    for (int j = 0; j < K; ++j) vq[j] -= fill[j];
+    const int n_old = n;
+    if (m > 0) {
+        const bool touch = lane_touches<K>(0, n_old - m);
+        field_drop_front<K>(sd.px(), vpx, m, touch);
+        field_drop_front<K>(sd.qty(), vq, m, touch);
+        field_drop_front<K>(sd.oid(), vo, m, touch);
+        field_drop_front<K>(sd.tid(), vt, m, touch);
+        int64_t vtm[K];
+        ld_vec<K>(sd.tm(), vtm);
+        field_drop_front<K>(sd.tm(), vtm, m, touch);
+        n = n_old - m;
+    } else if (nf > 0) {
+        // only slot 0 was partly filled
+        if (l == 0) sd.qty()[0] = vq[0];
+    }
+    return Q - F;
+}
+
+// Message dispatch (Sec. 4.2).  `book` points at the book in shared memory,
+// n[0] / n[1] are the bid / ask counts (warp-uniform).
+template <int K>
+__device__ __forceinline__ void process_message(char* book, int& n_bid, int& n_ask, int cap,
+                                                int rule, const Msg& m, TradeSink& ts,
+                                                Counters& ctr)
+{
+    SideRef<K, 0> bids{book};
+    SideRef<K, 1> asks{book + Geo<K>::SIDE_BYTES};
+    const int32_t T = m.type;
+    if (T == 0) {
+        ctr.add(CTR_NOOP, 1);
+        return;
+    }
+    if (T < 0 || T > 4 || (m.side != 1 && m.side != -1) || m.qty <= 0 ||
+        (T == 1 && m.price <= 0)) {
+        ctr.add(CTR_INVALID, 1);
+        return;
+    }
+    if (T == 1) {  // limit: match against the opposite side, then rest the remainder
+        ctr.add(CTR_LIMIT, 1);
+        ctr.add(CTR_LIMIT_QTY, m.qty);
+        int32_t rest = m.qty;
+        if (m.side == 1) {
+            if (n_ask > 0 && SideRef<K, 1>::at_least(asks.px()[0], m.price))
+                rest = match_order<K, 1>(asks, n_ask, m.price, rest, m.oid, m.tid, m.time_ns, ts, ctr);
+            if (rest > 0)
+                add_order<K, 0>(bids, n_bid, cap, rule, m.price, rest, m.oid, m.tid, m.time_ns, ctr);
+        } else {
+            if (n_bid > 0 && SideRef<K, 0>::at_least(bids.px()[0], m.price))
+                rest = match_order<K, 0>(bids, n_bid, m.price, rest, m.oid, m.tid, m.time_ns, ts, ctr);
+            if (rest > 0)
+                add_order<K, 1>(asks, n_ask, cap, rule, m.price, rest, m.oid, m.tid, m.time_ns, ctr);
+        }
+    } else if (T == 4) {  // market: price 0 (sell) / max_int (buy), remainder dropped
+        ctr.add(CTR_MARKET, 1);
+        ctr.add(CTR_MARKET_QTY, m.qty);
+        int32_t rest = m.qty;
+        if (m.side == 1) {
+            if (n_ask > 0)
+                rest = match_order<K, 1>(asks, n_ask, kMaxInt, rest, m.oid, m.tid, m.time_ns, ts, ctr);
+        } else {
+            if (n_bid > 0)
+                rest = match_order<K, 0>(bids, n_bid, 0, rest, m.oid, m.tid, m.time_ns, ts, ctr);
+        }
+        ctr.add(CTR_MARKET_DISCARDED_QTY, rest);
+    } else {  // cancel and delete are treated identically
+        ctr.add(CTR_CANCEL, 1);
+        if (m.side == 1)
+            cancel_order<K, 0>(bids, n_bid, m.oid, m.qty, ctr);
+        else
+            cancel_order<K, 1>(asks, n_ask, m.oid, m.qty, ctr);
+    }
+    __syncwarp();
+}
+
+}  // namespace lob

@@ -1,0 +1,759 @@
+// lob_engine.cu -- kernels and C ABI of the batched order-book engine.
+//
+// Processing kernel: a persistent grid of warps; each warp pulls a work item
+// (one book's message segment, Sec. 4.3 batching over independent books) from
+// a device work queue, stages the book and the segment's messages in shared
+// memory with 1-D bulk asynchronous copies (double-buffered chunks completed on
+// mbarriers), applies the messages in order with the warp routines of
+// lob_core.cuh, and writes the book back.  Uneven segment lengths balance
+// through the queue; the queue resets itself when the last warp leaves.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/lob.h"
+#include "lob_core.cuh"
+#include "lob_engine.h"
+
+using namespace lob;
+
+static_assert(sizeof(lob_msg_t) == sizeof(Msg), "lob_msg_t layout");
+static_assert(sizeof(lob_trade_t) == sizeof(Trade), "lob_trade_t layout");
+static_assert(LOB_N_COUNTERS == kNumCtr, "counter count");
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+void lob_set_error(const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int lob_cuda_fail(cudaError_t e, const char* where)
+{
+    lob_set_error("%s: %s", where, cudaGetErrorString(e));
+    return LOB_E_CUDA;
+}
+
+// ------------------------------------------------------------------ kernels
+
+namespace {
+
+constexpr uint64_t kWaitNs = 2000000000ull;  // bounded wait for a staged chunk: 2 s
+
+struct ProcArgs {
+    const Msg* msgs;
+    const int64_t* offsets;
+    const int32_t* book_ids;
+    int32_t n_items;
+    int32_t n_books;
+    char* state;
+    int32_t* counts;
+    Trade* trades;
+    int64_t* tcounts;
+    int64_t* stats;
+    int32_t* status;
+    int32_t* queue;
+    int32_t cap, rule, trade_cap, append, chunk, pad_;
+    uint64_t wait_ns;
+};
+
+template <int K>
+__host__ __device__ constexpr int warp_smem_bytes(int chunk)
+{
+    return ((Geo<K>::BOOK_BYTES + 2 * chunk * 32 + 16) + 127) / 128 * 128;
+}
+
+// threads per CTA the processing kernel is compiled for (bounds registers)
+template <int K>
+constexpr int max_threads() { return K >= 8 ? 256 : 512; }
+
+__device__ __forceinline__ Msg load_msg(const Msg* p)
+{
+    const int4* q = reinterpret_cast<const int4*>(p);
+    int4 a = q[0], b = q[1];
+    Msg m;
+    m.type = a.x; m.side = a.y; m.price = a.z; m.qty = a.w;
+    m.oid = b.x; m.tid = b.y;
+    m.time_ns = (int64_t)(((uint64_t)(uint32_t)b.w << 32) | (uint32_t)b.z);
+    return m;
+}
+
+template <int K>
+__global__ void __launch_bounds__(max_threads<K>()) k_process(ProcArgs a)
+{
+    extern __shared__ __align__(128) char smem[];
+    const int l = lane_id();
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int chunk = a.chunk;
+    char* base = smem + warp * warp_smem_bytes<K>(chunk);
+    char* book = base;
+    char* msgbuf = base + Geo<K>::BOOK_BYTES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk * 32);
+    const int total_warps = gridDim.x * W;
+
+    if (l == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    __syncwarp();
+
+    uint32_t g = 0;  // chunks consumed by this warp: stage g&1, parity (g>>1)&1
+    bool failed = false;
+    while (!failed) {
+        int item = 0;
+        if (l == 0) item = atomicAdd(&a.queue[0], 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= a.n_items) break;
+        const int b = a.book_ids ? a.book_ids[item] : item;
+        if (b < 0 || b >= a.n_books) {
+            if (l == 0) atomicOr(a.status, LOB_STATUS_BAD_BOOK);
+            continue;
+        }
+        const int64_t lo = a.offsets[item], hi = a.offsets[item + 1];
+        if (hi < lo) {
+            if (l == 0) atomicOr(a.status, LOB_STATUS_BAD_SEGMENT);
+            continue;
+        }
+        TradeSink ts{a.trades + (int64_t)b * a.trade_cap, a.append ? a.tcounts[b] : 0,
+                     a.trade_cap};
+        const int64_t nmsg = hi - lo;
+        if (nmsg == 0) {
+            __syncwarp();
+            if (l == 0) a.tcounts[b] = ts.count;
+            continue;
+        }
+        const int nchunks = (int)((nmsg + chunk - 1) / chunk);
+        char* gbook = a.state + (int64_t)b * Geo<K>::BOOK_BYTES;
+        if (l == 0) {
+            fence_proxy_async();
+            for (int c = 0; c < 2 && c < nchunks; ++c) {
+                const uint32_t st = (g + c) & 1;
+                const int64_t c0 = lo + (int64_t)c * chunk;
+                const uint32_t cnt = (uint32_t)min((int64_t)chunk, hi - c0);
+                mbar_expect_tx(&bar[st], cnt * 32 + (c == 0 ? Geo<K>::BOOK_BYTES : 0));
+                if (c == 0) bulk_g2s(book, gbook, Geo<K>::BOOK_BYTES, &bar[st]);
+                bulk_g2s(msgbuf + st * chunk * 32, a.msgs + c0, cnt * 32, &bar[st]);
+            }
+        }
+        int n_bid = a.counts[2 * b], n_ask = a.counts[2 * b + 1];
+        Counters ctr{0, l};
+        for (int c = 0; c < nchunks; ++c) {
+            const uint32_t st = (g + c) & 1, par = ((g + c) >> 1) & 1;
+            if (!mbar_wait_bounded(&bar[st], par, a.wait_ns)) {
+                // give up on this warp: record it, let in-flight copies land
+                if (l == 0) atomicOr(a.status, LOB_STATUS_TIMEOUT);
+                const int last = min(c + 1, nchunks - 1);
+                for (int d = c; d <= last; ++d)
+                    mbar_wait_bounded(&bar[(g + d) & 1], ((g + d) >> 1) & 1, a.wait_ns);
+                failed = true;
+                break;
+            }
+            const Msg* mb = reinterpret_cast<const Msg*>(msgbuf + st * chunk * 32);
+            const int cnt = (int)min((int64_t)chunk, hi - (lo + (int64_t)c * chunk));
+            for (int i = 0; i < cnt; ++i) {
+                const Msg m = load_msg(mb + i);
+                process_message<K>(book, n_bid, n_ask, a.cap, a.rule, m, ts, ctr);
+            }
+            __syncwarp();
+            if (c + 2 < nchunks && l == 0) {
+                fence_proxy_async();
+                const int64_t c0 = lo + (int64_t)(c + 2) * chunk;
+                const uint32_t cn = (uint32_t)min((int64_t)chunk, hi - c0);
+                mbar_expect_tx(&bar[st], cn * 32);
+                bulk_g2s(msgbuf + st * chunk * 32, a.msgs + c0, cn * 32, &bar[st]);
+            }
+        }
+        if (failed) break;
+        g += (uint32_t)nchunks;
+        // write the book back
+        const int4* src = reinterpret_cast<const int4*>(book);
+        int4* dst = reinterpret_cast<int4*>(gbook);
+#pragma unroll 4
+        for (int i = l; i < Geo<K>::BOOK_BYTES / 16; i += 32) dst[i] = src[i];
+        ctr.add(CTR_MSGS, nmsg);
+        if (l < kNumCtr) a.stats[(int64_t)b * kNumCtr + l] += ctr.v;
+        if (l == 0) {
+            a.counts[2 * b] = n_bid;
+            a.counts[2 * b + 1] = n_ask;
+            a.tcounts[b] = ts.count;
+        }
+        __syncwarp();
+    }
+    // leave the queue; the last warp out resets it for the next launch
+    if (l == 0) {
+        __threadfence();
+        const int done = atomicAdd(&a.queue[1], 1);
+        if (done == total_warps - 1) {
+            a.queue[0] = 0;
+            a.queue[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+// Top `depth` levels of every book (warp per book, both sides).
+template <int K>
+__global__ void k_levels(const char* __restrict__ state, const int32_t* __restrict__ counts,
+                         int32_t n_books, int32_t depth, int32_t* bid_px, int32_t* bid_qty,
+                         int32_t* ask_px, int32_t* ask_qty)
+{
+    __shared__ unsigned long long lq[8][64];
+    __shared__ int32_t lp[8][64];
+    const int l = lane_id(), w = threadIdx.x >> 5;
+    const int b = blockIdx.x * (blockDim.x >> 5) + w;
+    if (b >= n_books) return;
+    for (int x = 0; x < 2; ++x) {
+        const char* side = state + (int64_t)b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
+        const int32_t* px = reinterpret_cast<const int32_t*>(side + Geo<K>::PX);
+        const int32_t* q = reinterpret_cast<const int32_t*>(side + Geo<K>::QTY);
+        const int n = counts[2 * b + x];
+        int32_t vpx[K], vq[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            vpx[j] = px[l * K + j];
+            vq[j] = q[l * K + j];
+        }
+        for (int k = l; k < depth; k += 32) {
+            lq[w][k] = 0;
+            lp[w][k] = -1;
+        }
+        __syncwarp();
+        const int32_t prev = __shfl_up_sync(kFull, vpx[K - 1], 1);
+        bool start[K];
+        int before = 0;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int s = l * K + j;
+            const int32_t left = j == 0 ? prev : vpx[j - 1];
+            start[j] = s < n && (s == 0 || vpx[j] != left);
+            const unsigned bal = __ballot_sync(kFull, start[j]);
+            before += __popc(bal & ((1u << l) - 1u));
+        }
+        int lvl = before - 1;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int s = l * K + j;
+            lvl += start[j] ? 1 : 0;
+            if (s < n && lvl < depth) {
+                atomicAdd(&lq[w][lvl], (unsigned long long)vq[j]);
+                if (start[j]) lp[w][lvl] = vpx[j];
+            }
+        }
+        __syncwarp();
+        int32_t* opx = (x == 0 ? bid_px : ask_px) + (int64_t)b * depth;
+        int32_t* oq = (x == 0 ? bid_qty : ask_qty) + (int64_t)b * depth;
+        for (int k = l; k < depth; k += 32) {
+            opx[k] = lp[w][k];
+            oq[k] = (int32_t)min(lq[w][k], (unsigned long long)kMaxInt);
+        }
+        __syncwarp();
+    }
+}
+
+// Canonical dump: thread per (book, side, slot < cap).
+template <int K>
+__global__ void k_get_book(const char* __restrict__ state, const int32_t* __restrict__ counts,
+                           int32_t n_books, int32_t cap, int32_t* px, int32_t* qty, int32_t* oid,
+                           int32_t* tid, int64_t* tm, int32_t* count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)n_books * 2 * cap;
+    if (i >= total) return;
+    const int s = (int)(i % cap);
+    const int64_t bx = i / cap;  // book*2 + side
+    const int x = (int)(bx & 1);
+    const int64_t b = bx >> 1;
+    const char* side = state + b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
+    const bool live = s < counts[bx];
+    if (px) px[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::PX)[s] : -1;
+    if (qty) qty[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::QTY)[s] : -1;
+    if (oid) oid[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::OID)[s] : -1;
+    if (tid) tid[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::TID)[s] : -1;
+    if (tm) tm[i] = live ? reinterpret_cast<const int64_t*>(side + Geo<K>::TM)[s] : -1;
+    if (count && s == 0) count[bx] = counts[bx];
+}
+
+// Load books from the canonical layout; warp per (book, side).
+template <int K>
+__global__ void k_set_book(char* state, int32_t* counts, int32_t n_books, int32_t cap,
+                           const int32_t* __restrict__ px, const int32_t* __restrict__ qty,
+                           const int32_t* __restrict__ oid, const int32_t* __restrict__ tid,
+                           const int64_t* __restrict__ tm, const int32_t* __restrict__ count,
+                           int32_t* status)
+{
+    const int l = lane_id();
+    const int64_t bx = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (bx >= (int64_t)n_books * 2) return;
+    const int x = (int)(bx & 1);
+    const int64_t b = bx >> 1;
+    int n = count[bx];
+    const int64_t base = bx * cap;
+    bool bad = n < 0 || n > cap;
+    if (!bad) {
+        for (int s = l; s < n; s += 32) {
+            const int32_t p = px[base + s];
+            bool ok = p > 0 && qty[base + s] > 0;
+            if (s > 0) {
+                const int32_t pp = px[base + s - 1];
+                ok = ok && (x == 0 ? p <= pp : p >= pp);
+            }
+            if (!ok) bad = true;
+        }
+    }
+    bad = __any_sync(kFull, bad);
+    if (bad) {
+        n = 0;
+        if (l == 0) atomicOr(status, LOB_STATUS_BAD_BOOK_LOAD);
+    }
+    char* side = state + b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
+    for (int s = l; s < n; s += 32) {
+        reinterpret_cast<int32_t*>(side + Geo<K>::PX)[s] = px[base + s];
+        reinterpret_cast<int32_t*>(side + Geo<K>::QTY)[s] = qty[base + s];
+        reinterpret_cast<int32_t*>(side + Geo<K>::OID)[s] = oid[base + s];
+        reinterpret_cast<int32_t*>(side + Geo<K>::TID)[s] = tid[base + s];
+        reinterpret_cast<int64_t*>(side + Geo<K>::TM)[s] = tm[base + s];
+    }
+    if (l == 0) counts[bx] = n;
+}
+
+__global__ void k_get_trades(const Trade* __restrict__ log, const int64_t* __restrict__ tcounts,
+                             int32_t n_books, int32_t cap, Trade* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)n_books * cap) return;
+    const int64_t b = i / cap, j = i % cap;
+    const int4* src = reinterpret_cast<const int4*>(log + i);
+    int4* dst = reinterpret_cast<int4*>(out + i);
+    if (j < tcounts[b]) {
+        dst[0] = src[0];
+        dst[1] = src[1];
+    } else {
+        dst[0] = make_int4(-1, -1, -1, -1);
+        dst[1] = make_int4(-1, -1, -1, -1);
+    }
+}
+
+// ---------------------------------------------------------- dispatch by K
+
+int k_of(int capacity)
+{
+    if (capacity <= 32) return 1;
+    if (capacity <= 64) return 2;
+    if (capacity <= 128) return 4;
+    if (capacity <= 256) return 8;
+    return 16;
+}
+
+const void* process_kernel(int K)
+{
+    switch (K) {
+    case 1: return reinterpret_cast<const void*>(&k_process<1>);
+    case 2: return reinterpret_cast<const void*>(&k_process<2>);
+    case 4: return reinterpret_cast<const void*>(&k_process<4>);
+    case 8: return reinterpret_cast<const void*>(&k_process<8>);
+    default: return reinterpret_cast<const void*>(&k_process<16>);
+    }
+}
+
+int smem_per_warp(int K, int chunk)
+{
+    switch (K) {
+    case 1: return warp_smem_bytes<1>(chunk);
+    case 2: return warp_smem_bytes<2>(chunk);
+    case 4: return warp_smem_bytes<4>(chunk);
+    case 8: return warp_smem_bytes<8>(chunk);
+    default: return warp_smem_bytes<16>(chunk);
+    }
+}
+
+int max_warps(int K) { return K >= 8 ? 8 : 16; }
+
+}  // namespace
+
+int lob_book_bytes(int K) { return 48 * 32 * K; }
+
+// ---------------------------------------------------------- internal API
+
+int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                       const int32_t* d_book_ids, int32_t n_active, int append,
+                       cudaStream_t stream)
+{
+    if (n_active == 0) return LOB_OK;
+    ProcArgs a;
+    a.msgs = reinterpret_cast<const Msg*>(d_msgs);
+    a.offsets = d_offsets;
+    a.book_ids = d_book_ids;
+    a.n_items = n_active;
+    a.n_books = c->cfg.n_books;
+    a.state = c->d_state;
+    a.counts = c->d_counts;
+    a.trades = reinterpret_cast<Trade*>(c->d_trades);
+    a.tcounts = c->d_tcounts;
+    a.stats = c->d_stats;
+    a.status = c->d_status;
+    a.queue = c->d_queue;
+    a.cap = c->cfg.capacity;
+    a.rule = c->cfg.overflow_rule;
+    a.trade_cap = c->cfg.trade_capacity;
+    a.append = append;
+    a.chunk = c->chunk;
+    a.pad_ = 0;
+    a.wait_ns = kWaitNs;
+    const int W = c->warps_per_cta;
+    int grid = (n_active + W - 1) / W;
+    const int resident = c->num_sms * c->ctas_per_sm_eff;
+    if (grid > resident) grid = resident;
+    if (grid < 1) grid = 1;
+    void* args[] = {&a};
+    cudaError_t e = cudaLaunchKernel(process_kernel(c->K), dim3(grid), dim3(32 * W), args,
+                                     (size_t)c->smem_per_cta, stream);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_process_batch launch");
+    c->launches += 1;
+    return LOB_OK;
+}
+
+static int configure_launch(lob_ctx* c, int W, int chunk, int ctas_per_sm)
+{
+    if (W > max_warps(c->K)) {
+        lob_set_error("at capacity %d at most %d warps per CTA", c->cfg.capacity, max_warps(c->K));
+        return LOB_E_INVAL;
+    }
+    const int smem = smem_per_warp(c->K, chunk) * W;
+    int max_optin = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                           c->device);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "cudaDeviceGetAttribute");
+    if (smem > max_optin) {
+        lob_set_error("launch shape needs %d B of shared memory per CTA (max %d)", smem, max_optin);
+        return LOB_E_INVAL;
+    }
+    const void* fn = process_kernel(c->K);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * W, smem);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) {
+        lob_set_error("launch shape does not fit on an SM");
+        return LOB_E_INVAL;
+    }
+    c->warps_per_cta = W;
+    c->chunk = chunk;
+    c->ctas_per_sm = ctas_per_sm;
+    c->ctas_per_sm_eff = ctas_per_sm > 0 ? (ctas_per_sm < per_sm ? ctas_per_sm : per_sm) : per_sm;
+    c->smem_per_cta = smem;
+    return LOB_OK;
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int lob_abi_version(void) { return 1; }
+
+const char* lob_last_error(void) { return g_err.c_str(); }
+
+int64_t lob_launch_count(const lob_ctx* c) { return c ? c->launches : -1; }
+
+int lob_create(lob_ctx** out, const lob_config_t* cfg, void* stream)
+{
+    if (!out || !cfg) {
+        lob_set_error("lob_create: null argument");
+        return LOB_E_INVAL;
+    }
+    if (cfg->n_books < 1 || cfg->capacity < 1 || cfg->capacity > 32 * kMaxK ||
+        cfg->trade_capacity < 0 || (cfg->overflow_rule != 0 && cfg->overflow_rule != 1) ||
+        (cfg->flags & ~LOB_FLAG_APPEND_TRADES)) {
+        lob_set_error("lob_create: invalid configuration (n_books=%d capacity=%d "
+                      "trade_capacity=%d overflow_rule=%d flags=%d)",
+                      cfg->n_books, cfg->capacity, cfg->trade_capacity, cfg->overflow_rule,
+                      cfg->flags);
+        return LOB_E_INVAL;
+    }
+    lob_ctx* c = new (std::nothrow) lob_ctx();
+    if (!c) {
+        lob_set_error("lob_create: host allocation failed");
+        return LOB_E_NOMEM;
+    }
+    c->cfg = *cfg;
+    c->K = k_of(cfg->capacity);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return lob_cuda_fail(e, "lob_create");
+    }
+    const int64_t nb = cfg->n_books;
+    const size_t state_b = (size_t)nb * lob_book_bytes(c->K);
+    const size_t trade_b = (size_t)nb * (size_t)cfg->trade_capacity * sizeof(lob_trade_t);
+    struct {
+        void** p;
+        size_t bytes;
+    } allocs[] = {{(void**)&c->d_state, state_b},
+                  {(void**)&c->d_counts, (size_t)nb * 2 * sizeof(int32_t)},
+                  {(void**)&c->d_trades, trade_b > 0 ? trade_b : 32},
+                  {(void**)&c->d_tcounts, (size_t)nb * sizeof(int64_t)},
+                  {(void**)&c->d_stats, (size_t)nb * kNumCtr * sizeof(int64_t)},
+                  {(void**)&c->d_status, 64},
+                  {(void**)&c->d_queue, 64}};
+    for (auto& al : allocs) {
+        e = cudaMalloc(al.p, al.bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            lob_destroy(c);
+            lob_set_error("lob_create: cudaMalloc of %zu bytes failed", al.bytes);
+            return LOB_E_NOMEM;
+        }
+    }
+    e = cudaMemsetAsync(c->d_state, 0, state_b, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counts, 0, (size_t)nb * 2 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_tcounts, 0, (size_t)nb * sizeof(int64_t), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->d_stats, 0, (size_t)nb * kNumCtr * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 64, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_queue, 0, 64, s);
+    if (e != cudaSuccess) {
+        lob_destroy(c);
+        return lob_cuda_fail(e, "lob_create memset");
+    }
+    int rc = configure_launch(c, c->K >= 8 ? 4 : 8, 64, 0);
+    if (rc != LOB_OK) {
+        lob_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LOB_OK;
+}
+
+int lob_destroy(lob_ctx* c)
+{
+    if (!c) return LOB_OK;
+    cudaError_t first = cudaSuccess;
+    if (c->d_state || c->d_trades) first = cudaDeviceSynchronize();
+    void* ptrs[] = {c->d_state, c->d_counts, c->d_trades, c->d_tcounts,
+                    c->d_stats, c->d_status, c->d_queue};
+    for (void* p : ptrs)
+        if (p) {
+            cudaError_t e = cudaFree(p);
+            if (first == cudaSuccess) first = e;
+        }
+    delete c;
+    if (first != cudaSuccess) return lob_cuda_fail(first, "lob_destroy");
+    return LOB_OK;
+}
+
+int lob_reset(lob_ctx* c, void* stream)
+{
+    if (!c) {
+        lob_set_error("lob_reset: null context");
+        return LOB_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t nb = c->cfg.n_books;
+    cudaError_t e = cudaMemsetAsync(c->d_counts, 0, (size_t)nb * 2 * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_tcounts, 0, (size_t)nb * sizeof(int64_t), s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(c->d_stats, 0, (size_t)nb * kNumCtr * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 64, s);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_reset");
+    return LOB_OK;
+}
+
+static int check_batch(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                       const int32_t* d_book_ids, int32_t n_active, const char* who)
+{
+    if (!c) {
+        lob_set_error("%s: null context", who);
+        return LOB_E_INVAL;
+    }
+    if (n_active < 0 || n_active > c->cfg.n_books) {
+        lob_set_error("%s: n_active=%d outside [0, %d]", who, n_active, c->cfg.n_books);
+        return LOB_E_INVAL;
+    }
+    if (n_active == 0) return LOB_OK;
+    if (!d_book_ids && n_active != c->cfg.n_books) {
+        lob_set_error("%s: without book ids every book needs a segment (n_active=%d, n_books=%d)",
+                      who, n_active, c->cfg.n_books);
+        return LOB_E_INVAL;
+    }
+    if (!d_msgs || !d_offsets) {
+        lob_set_error("%s: null message or offset pointer", who);
+        return LOB_E_INVAL;
+    }
+    if (((uintptr_t)d_msgs & 15u) != 0) {
+        lob_set_error("%s: messages must be 16-byte aligned", who);
+        return LOB_E_INVAL;
+    }
+    return LOB_OK;
+}
+
+int lob_process_batch(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                      const int32_t* d_book_ids, int32_t n_active, void* stream)
+{
+    int rc = check_batch(c, d_msgs, d_offsets, d_book_ids, n_active, "lob_process_batch");
+    if (rc != LOB_OK) return rc;
+    const int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
+    return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, append,
+                              (cudaStream_t)stream);
+}
+
+int lob_inject_orders(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                      const int32_t* d_book_ids, int32_t n_active, void* stream)
+{
+    int rc = check_batch(c, d_msgs, d_offsets, d_book_ids, n_active, "lob_inject_orders");
+    if (rc != LOB_OK) return rc;
+    return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, 1,
+                              (cudaStream_t)stream);
+}
+
+int lob_clear_trades(lob_ctx* c, void* stream)
+{
+    if (!c) {
+        lob_set_error("lob_clear_trades: null context");
+        return LOB_E_INVAL;
+    }
+    cudaError_t e = cudaMemsetAsync(c->d_tcounts, 0, (size_t)c->cfg.n_books * sizeof(int64_t),
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_clear_trades");
+    return LOB_OK;
+}
+
+#define LOB_DISPATCH_K(KV, CALL)                      \
+    switch (KV) {                                     \
+    case 1: { constexpr int KK = 1; CALL; } break;    \
+    case 2: { constexpr int KK = 2; CALL; } break;    \
+    case 4: { constexpr int KK = 4; CALL; } break;    \
+    case 8: { constexpr int KK = 8; CALL; } break;    \
+    default: { constexpr int KK = 16; CALL; } break;  \
+    }
+
+int lob_get_levels(lob_ctx* c, int32_t depth, int32_t* d_bid_px, int32_t* d_bid_qty,
+                   int32_t* d_ask_px, int32_t* d_ask_qty, void* stream)
+{
+    if (!c || depth < 1 || depth > 64 || !d_bid_px || !d_bid_qty || !d_ask_px || !d_ask_qty) {
+        lob_set_error("lob_get_levels: invalid argument (depth=%d)", depth);
+        return LOB_E_INVAL;
+    }
+    const int wpb = 8;
+    dim3 grid((c->cfg.n_books + wpb - 1) / wpb), block(32 * wpb);
+    cudaStream_t s = (cudaStream_t)stream;
+    LOB_DISPATCH_K(c->K, (k_levels<KK><<<grid, block, 0, s>>>(c->d_state, c->d_counts,
+                                                              c->cfg.n_books, depth, d_bid_px,
+                                                              d_bid_qty, d_ask_px, d_ask_qty)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_get_levels");
+    c->launches += 1;
+    return LOB_OK;
+}
+
+int lob_get_trades(lob_ctx* c, lob_trade_t* d_out, int64_t* d_counts, void* stream)
+{
+    if (!c) {
+        lob_set_error("lob_get_trades: null context");
+        return LOB_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (d_out && c->cfg.trade_capacity > 0) {
+        const int64_t n = (int64_t)c->cfg.n_books * c->cfg.trade_capacity;
+        k_get_trades<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const Trade*>(c->d_trades), c->d_tcounts, c->cfg.n_books,
+            c->cfg.trade_capacity, reinterpret_cast<Trade*>(d_out));
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return lob_cuda_fail(e, "lob_get_trades");
+        c->launches += 1;
+    }
+    if (d_counts) {
+        cudaError_t e = cudaMemcpyAsync(d_counts, c->d_tcounts,
+                                        (size_t)c->cfg.n_books * sizeof(int64_t),
+                                        cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return lob_cuda_fail(e, "lob_get_trades counts");
+    }
+    return LOB_OK;
+}
+
+int lob_get_book(lob_ctx* c, int32_t* px, int32_t* qty, int32_t* oid, int32_t* tid, int64_t* tm,
+                 int32_t* count, void* stream)
+{
+    if (!c) {
+        lob_set_error("lob_get_book: null context");
+        return LOB_E_INVAL;
+    }
+    const int64_t n = (int64_t)c->cfg.n_books * 2 * c->cfg.capacity;
+    dim3 grid((unsigned)((n + 255) / 256)), block(256);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int cap = c->cfg.capacity, nb = c->cfg.n_books;
+    LOB_DISPATCH_K(c->K, (k_get_book<KK><<<grid, block, 0, s>>>(c->d_state, c->d_counts, nb, cap,
+                                                                px, qty, oid, tid, tm, count)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_get_book");
+    c->launches += 1;
+    return LOB_OK;
+}
+
+int lob_set_book(lob_ctx* c, const int32_t* px, const int32_t* qty, const int32_t* oid,
+                 const int32_t* tid, const int64_t* tm, const int32_t* count, void* stream)
+{
+    if (!c || !px || !qty || !oid || !tid || !tm || !count) {
+        lob_set_error("lob_set_book: null argument");
+        return LOB_E_INVAL;
+    }
+    const int wpb = 8;
+    const int64_t nw = (int64_t)c->cfg.n_books * 2;
+    dim3 grid((unsigned)((nw + wpb - 1) / wpb)), block(32 * wpb);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int cap = c->cfg.capacity, nb = c->cfg.n_books;
+    LOB_DISPATCH_K(c->K, (k_set_book<KK><<<grid, block, 0, s>>>(c->d_state, c->d_counts, nb, cap,
+                                                                px, qty, oid, tid, tm, count,
+                                                                c->d_status)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_set_book");
+    c->launches += 1;
+    return LOB_OK;
+}
+
+int lob_get_stats(lob_ctx* c, int64_t* d_counters, int32_t* d_status, void* stream)
+{
+    if (!c) {
+        lob_set_error("lob_get_stats: null context");
+        return LOB_E_INVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (d_counters)
+        e = cudaMemcpyAsync(d_counters, c->d_stats,
+                            (size_t)c->cfg.n_books * kNumCtr * sizeof(int64_t),
+                            cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && d_status)
+        e = cudaMemcpyAsync(d_status, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_get_stats");
+    return LOB_OK;
+}
+
+int lob_set_launch(lob_ctx* c, int32_t warps_per_cta, int32_t chunk_msgs, int32_t ctas_per_sm)
+{
+    if (!c || warps_per_cta < 1 || warps_per_cta > 16 || chunk_msgs < 8 || chunk_msgs > 1024 ||
+        (chunk_msgs % 8) != 0 || ctas_per_sm < 0) {
+        lob_set_error("lob_set_launch: invalid shape (warps=%d chunk=%d ctas_per_sm=%d)",
+                      warps_per_cta, chunk_msgs, ctas_per_sm);
+        return LOB_E_INVAL;
+    }
+    return configure_launch(c, warps_per_cta, chunk_msgs, ctas_per_sm);
+}
+
+}  // extern "C"

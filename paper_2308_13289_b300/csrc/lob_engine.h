@@ -1,0 +1,35 @@
+// lob_engine.h -- context layout shared by the engine's translation units
+// (book engine and execution environment).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lob.h"
+
+struct lob_ctx {
+    lob_config_t cfg;
+    int device = 0;
+    int num_sms = 0;
+    int K = 4;                        // slots per lane: capacity rounded up to 32*K
+    char* d_state = nullptr;          // [n_books][48*32*K] book state (priority-sorted sides)
+    int32_t* d_counts = nullptr;      // [n_books][2] orders per side
+    lob_trade_t* d_trades = nullptr;  // [n_books][trade_capacity]
+    int64_t* d_tcounts = nullptr;     // [n_books] trades in the current log
+    int64_t* d_stats = nullptr;       // [n_books][LOB_N_COUNTERS]
+    int32_t* d_status = nullptr;      // status word (LOB_STATUS_*)
+    int32_t* d_queue = nullptr;       // work queue: [0] next item, [1] warps finished
+    int warps_per_cta = 8;
+    int chunk = 64;
+    int ctas_per_sm = 0;
+    int ctas_per_sm_eff = 1;
+    int smem_per_cta = 0;
+    int64_t launches = 0;
+};
+
+void lob_set_error(const char* fmt, ...);
+int lob_cuda_fail(cudaError_t e, const char* where);
+int lob_book_bytes(int K);
+int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                       const int32_t* d_book_ids, int32_t n_active, int append,
+                       cudaStream_t stream);
