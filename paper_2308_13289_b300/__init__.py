@@ -1,0 +1,211 @@
+"""Batched price-time-priority limit-order-book engine for B300 (sm_103a).
+
+Thin binding over ``liblob.so`` (C ABI in ``include/lob.h``): every step of the
+path runs in the library's CUDA kernels; this module only marshals torch CUDA
+tensors (device memory) and the current torch stream into the calls.
+
+Record layouts on the device (torch ``int32`` tensors, 8 words per record):
+  message  [type, side, price, qty, oid, tid, time_lo, time_hi]   (Sec. 4.2)
+  trade    [price, qty, oid_aggr, oid_stand, tid_aggr, tid_stand, time_lo, time_hi]
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import LobConfig, LobError, check
+
+OVERFLOW_EVICT, OVERFLOW_REJECT = 0, 1
+FLAG_APPEND_TRADES = 1
+N_COUNTERS = 20
+COUNTERS = ["msgs", "limit", "cancel", "market", "noop", "invalid", "trades", "traded_qty",
+            "rested", "rejected", "rejected_qty", "evicted", "evicted_qty", "cancel_hit",
+            "cancelled_qty", "cancel_miss", "market_discarded_qty", "limit_qty", "market_qty",
+            "trades_dropped"]
+STATUS_TIMEOUT, STATUS_BAD_BOOK, STATUS_BAD_SEGMENT, STATUS_BAD_BOOK_LOAD = 1, 2, 4, 8
+
+MSG_DTYPE = np.dtype([("type", "<i4"), ("side", "<i4"), ("price", "<i4"), ("qty", "<i4"),
+                      ("oid", "<i4"), ("tid", "<i4"), ("time_ns", "<i8")])
+TRADE_DTYPE = np.dtype([("price", "<i4"), ("qty", "<i4"), ("oid_aggr", "<i4"),
+                        ("oid_stand", "<i4"), ("tid_aggr", "<i4"), ("tid_stand", "<i4"),
+                        ("time_ns", "<i8")])
+
+
+def lib():
+    return _abi.load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def messages_to_device(msgs: np.ndarray, device="cuda") -> torch.Tensor:
+    """numpy message records (32 B each) -> int32 [N, 8] CUDA tensor."""
+    a = np.ascontiguousarray(msgs).view(np.int32).reshape(-1, 8)
+    return torch.from_numpy(a).to(device)
+
+
+def trades_to_numpy(t: torch.Tensor) -> np.ndarray:
+    """int32 [..., 8] trade tensor -> numpy structured records."""
+    a = np.ascontiguousarray(t.cpu().numpy())
+    return a.view(TRADE_DTYPE).reshape(a.shape[:-1])
+
+
+# ------------------------------------------------------------------ raw C ABI (same names)
+
+def lob_create(n_books, capacity, trade_capacity, overflow_rule=0, flags=0, stream=None):
+    h = ctypes.c_void_p()
+    cfg = LobConfig(n_books, capacity, trade_capacity, overflow_rule, flags)
+    check(lib().lob_create(ctypes.byref(h), ctypes.byref(cfg), _stream(stream)), "lob_create")
+    return h
+
+
+def lob_destroy(h):
+    check(lib().lob_destroy(h), "lob_destroy")
+
+
+def lob_reset(h, stream=None):
+    check(lib().lob_reset(h, _stream(stream)), "lob_reset")
+
+
+def lob_process_batch(h, msgs, offsets, book_ids=None, n_active=None, stream=None):
+    n = (offsets.numel() - 1) if n_active is None else n_active
+    check(lib().lob_process_batch(h, _ptr(msgs), _ptr(offsets), _ptr(book_ids), n,
+                                  _stream(stream)), "lob_process_batch")
+
+
+def lob_inject_orders(h, msgs, offsets, book_ids=None, n_active=None, stream=None):
+    n = (offsets.numel() - 1) if n_active is None else n_active
+    check(lib().lob_inject_orders(h, _ptr(msgs), _ptr(offsets), _ptr(book_ids), n,
+                                  _stream(stream)), "lob_inject_orders")
+
+
+def lob_clear_trades(h, stream=None):
+    check(lib().lob_clear_trades(h, _stream(stream)), "lob_clear_trades")
+
+
+def lob_get_levels(h, depth, bid_px, bid_qty, ask_px, ask_qty, stream=None):
+    check(lib().lob_get_levels(h, depth, _ptr(bid_px), _ptr(bid_qty), _ptr(ask_px),
+                               _ptr(ask_qty), _stream(stream)), "lob_get_levels")
+
+
+def lob_get_trades(h, out, counts, stream=None):
+    check(lib().lob_get_trades(h, _ptr(out), _ptr(counts), _stream(stream)), "lob_get_trades")
+
+
+def lob_get_book(h, px, qty, oid, tid, tm, count, stream=None):
+    check(lib().lob_get_book(h, _ptr(px), _ptr(qty), _ptr(oid), _ptr(tid), _ptr(tm),
+                             _ptr(count), _stream(stream)), "lob_get_book")
+
+
+def lob_set_book(h, px, qty, oid, tid, tm, count, stream=None):
+    check(lib().lob_set_book(h, _ptr(px), _ptr(qty), _ptr(oid), _ptr(tid), _ptr(tm),
+                             _ptr(count), _stream(stream)), "lob_set_book")
+
+
+def lob_get_stats(h, counters, status, stream=None):
+    check(lib().lob_get_stats(h, _ptr(counters), _ptr(status), _stream(stream)), "lob_get_stats")
+
+
+def lob_set_launch(h, warps_per_cta, chunk_msgs, ctas_per_sm=0):
+    check(lib().lob_set_launch(h, warps_per_cta, chunk_msgs, ctas_per_sm), "lob_set_launch")
+
+
+def lob_launch_count(h):
+    return int(lib().lob_launch_count(h))
+
+
+# ------------------------------------------------------------------ convenience object
+
+class Engine:
+    """A lob_ctx with torch-allocated outputs.  All calls run on the current
+    torch stream unless `stream` is given."""
+
+    def __init__(self, n_books: int, capacity: int, trade_capacity: int,
+                 overflow_rule: int = OVERFLOW_EVICT, append_trades: bool = False,
+                 stream=None):
+        self.n_books, self.capacity, self.trade_capacity = n_books, capacity, trade_capacity
+        self.stream = stream
+        self.h = lob_create(n_books, capacity, trade_capacity, overflow_rule,
+                            FLAG_APPEND_TRADES if append_trades else 0, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lob_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        lob_reset(self.h, self.stream)
+
+    def process_batch(self, msgs, offsets, book_ids=None):
+        lob_process_batch(self.h, msgs, offsets, book_ids, stream=self.stream)
+
+    def inject_orders(self, msgs, offsets, book_ids=None):
+        lob_inject_orders(self.h, msgs, offsets, book_ids, stream=self.stream)
+
+    def clear_trades(self):
+        lob_clear_trades(self.h, self.stream)
+
+    def set_launch(self, warps_per_cta, chunk_msgs, ctas_per_sm=0):
+        lob_set_launch(self.h, warps_per_cta, chunk_msgs, ctas_per_sm)
+
+    def launch_count(self):
+        return lob_launch_count(self.h)
+
+    def levels(self, depth: int):
+        out = [torch.empty((self.n_books, depth), dtype=torch.int32, device="cuda")
+               for _ in range(4)]
+        lob_get_levels(self.h, depth, *out, stream=self.stream)
+        return tuple(out)
+
+    def trades(self):
+        out = torch.empty((self.n_books, max(self.trade_capacity, 0), 8), dtype=torch.int32,
+                          device="cuda")
+        cnt = torch.empty(self.n_books, dtype=torch.int64, device="cuda")
+        lob_get_trades(self.h, out if self.trade_capacity > 0 else None, cnt, self.stream)
+        return out, cnt
+
+    def book(self):
+        shp = (self.n_books, 2, self.capacity)
+        px, qty, oid, tid = (torch.empty(shp, dtype=torch.int32, device="cuda")
+                             for _ in range(4))
+        tm = torch.empty(shp, dtype=torch.int64, device="cuda")
+        cnt = torch.empty((self.n_books, 2), dtype=torch.int32, device="cuda")
+        lob_get_book(self.h, px, qty, oid, tid, tm, cnt, self.stream)
+        return dict(price=px, qty=qty, oid=oid, tid=tid, time_ns=tm, count=cnt)
+
+    def set_book(self, bk: dict):
+        t = {k: bk[k].contiguous() for k in ("price", "qty", "oid", "tid", "time_ns", "count")}
+        lob_set_book(self.h, t["price"], t["qty"], t["oid"], t["tid"], t["time_ns"], t["count"],
+                     self.stream)
+
+    def stats(self):
+        ctr = torch.empty((self.n_books, N_COUNTERS), dtype=torch.int64, device="cuda")
+        st = torch.empty(1, dtype=torch.int32, device="cuda")
+        lob_get_stats(self.h, ctr, st, self.stream)
+        return ctr, st
+
+
+__all__ = [n for n in dir() if n.startswith("lob_")] + [
+    "Engine", "LobError", "messages_to_device", "trades_to_numpy", "MSG_DTYPE", "TRADE_DTYPE",
+    "COUNTERS", "N_COUNTERS"]

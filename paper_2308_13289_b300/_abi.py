@@ -1,0 +1,67 @@
+"""ctypes declarations of the C ABI in include/lob.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblob.so")
+
+vp = ctypes.c_void_p
+i32 = ctypes.c_int32
+i64 = ctypes.c_int64
+
+
+class LobConfig(ctypes.Structure):
+    _fields_ = [("n_books", i32), ("capacity", i32), ("trade_capacity", i32),
+                ("overflow_rule", i32), ("flags", i32)]
+
+
+# name -> (restype, argtypes); every symbol of include/lob.h
+SIGNATURES = {
+    "lob_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(LobConfig), vp]),
+    "lob_destroy": (ctypes.c_int, [vp]),
+    "lob_reset": (ctypes.c_int, [vp, vp]),
+    "lob_process_batch": (ctypes.c_int, [vp, vp, vp, vp, i32, vp]),
+    "lob_inject_orders": (ctypes.c_int, [vp, vp, vp, vp, i32, vp]),
+    "lob_clear_trades": (ctypes.c_int, [vp, vp]),
+    "lob_get_levels": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp]),
+    "lob_get_trades": (ctypes.c_int, [vp, vp, vp, vp]),
+    "lob_get_book": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+    "lob_set_book": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+    "lob_get_stats": (ctypes.c_int, [vp, vp, vp, vp]),
+    "lob_set_launch": (ctypes.c_int, [vp, i32, i32, i32]),
+    "lob_launch_count": (i64, [vp]),
+    "lob_last_error": (ctypes.c_char_p, []),
+    "lob_abi_version": (ctypes.c_int, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load liblob.so; raises (never falls back) when it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("liblob.so is not built; run paper_2308_13289_b300.build.build() "
+                              "(the engine has no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class LobError(RuntimeError):
+    def __init__(self, code, where):
+        msg = load().lob_last_error()
+        super().__init__("%s failed (%d): %s" % (where, code, msg.decode() if msg else ""))
+        self.code = code
+
+
+def check(code, where):
+    if code != 0:
+        raise LobError(code, where)

@@ -1,0 +1,56 @@
+"""The engine library loads without a GPU and exports every entry point that
+include/*.h declares (no compute call is made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(lob_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2308_13289_b300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("lob_create", "lob_process_batch", "lob_inject_orders", "lob_get_levels",
+                 "lob_get_trades", "lob_destroy"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in sorted(declared_functions()):
+        assert hasattr(lib, name), "liblob.so does not export %s" % name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2308_13289_b300 import _abi
+    missing = declared_functions() - set(_abi.SIGNATURES)
+    assert not missing, missing
+
+
+def test_cpu_only_calls_fail_cleanly(lib):
+    lib.lob_abi_version.restype = ctypes.c_int
+    assert lib.lob_abi_version() == 1
+    lib.lob_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.lob_destroy(None) == 0
+    lib.lob_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.lob_create(None, None, None) == -1
+    lib.lob_last_error.restype = ctypes.c_char_p
+    assert b"null" in lib.lob_last_error()

@@ -1,0 +1,202 @@
+"""CUDA engine vs the CPU oracle, element by element, bit-exact.
+
+Covers the hand-worked examples, a brute-force corpus of tiny books, seeded
+streams of the paper-style workloads across capacities (K = 1..16 slots per
+lane), both full-side rules, several launch shapes (warps per CTA, staged
+chunk sizes), chunked calls, book subsets, ragged and empty segments, and the
+device status word."""
+import numpy as np
+import pytest
+import torch
+
+import lobgen
+import oracle
+from engine_harness import assert_same, gpu_outputs, oracle_outputs, run_both
+from golden_format import cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import paper_2308_13289_b300 as eng
+    from paper_2308_13289_b300 import build
+    build.build()
+    return eng
+
+
+def test_golden_examples_on_gpu(eng):
+    for c in cases():
+        m = c.message_array()
+        off = np.array([0, len(m)], np.int64)
+        g, r = run_both(m, off, c.capacity, c.trade_capacity, c.rule)
+        assert_same(g, r)
+
+
+def test_bruteforce_corpus_on_gpu(eng):
+    from test_oracle_bruteforce import _alphabet, _encode
+    alphabet = _alphabet()
+    rng = np.random.default_rng(11)
+    for cap, rule in ((1, 0), (2, 0), (3, 1), (5, 0)):
+        seqs = [tuple(r) for r in rng.integers(0, len(alphabet), size=(20_000, 8))]
+        m = _encode(seqs, alphabet)
+        off = np.arange(0, len(seqs) * 8 + 1, 8, dtype=np.int64)
+        g, r = run_both(m, off, cap, 8, rule)
+        assert_same(g, r)
+
+
+@pytest.mark.parametrize("cap", [1, 7, 33, 100, 128, 250, 500, 512])
+def test_seeded_streams_across_capacities(eng, cap):
+    p = lobgen.make_params(1000 + cap, "pm1")
+    counts = [3000, 1, 0, 2999, 4097, 64, 65, 500]
+    msgs, off = lobgen.generate(p, counts)
+    g, r = run_both(msgs, off, cap, 3000, 0, depth=12)
+    assert_same(g, r)
+
+
+def test_small_workload_reject_rule(eng):
+    w = lobgen.WORKLOADS["small_16x10k"]
+    msgs, off = lobgen.generate(lobgen.make_params(w["seed"], w["mid_walk"]), [w["msgs"]] * 16)
+    g, r = run_both(msgs, off, 100, 8192, 1)
+    assert_same(g, r)
+
+
+@pytest.mark.parametrize("launch", [(1, 8, 0), (4, 64, 0), (16, 256, 0), (8, 1024, 1), (2, 40, 2)])
+def test_launch_shapes(eng, launch):
+    w = lobgen.WORKLOADS["small_16x10k"]
+    msgs, off = lobgen.generate(lobgen.make_params(w["seed"], w["mid_walk"]), [w["msgs"]] * 16)
+    g, r = run_both(msgs, off, 100, 8192, 0, launch=launch)
+    assert_same(g, r)
+
+
+def test_trade_log_bound_counts_dropped(eng):
+    msgs, off = lobgen.generate(lobgen.make_params(5), [4000] * 6)
+    g, r = run_both(msgs, off, 100, 50, 0)
+    assert_same(g, r)
+    assert (r["counters"][:, oracle.COUNTERS.index("trades_dropped")] > 0).all()
+
+
+def test_chunked_calls_with_append_equal_one_call(eng):
+    """The plain form (one call per 100-message chunk, trades appended) gives
+    exactly the single-call result."""
+    n, per = 12, 2500
+    msgs, off = lobgen.generate(lobgen.make_params(77, "three"), [per] * n)
+    e = eng.Engine(n, 100, 4096, append_trades=True)
+    d = eng.messages_to_device(msgs)
+    for c0 in range(0, per, 100):
+        c1 = min(per, c0 + 100)
+        for b in range(n):
+            seg = torch.tensor([b * per + c0, b * per + c1], dtype=torch.int64, device="cuda")
+            ids = torch.tensor([b], dtype=torch.int32, device="cuda")
+            e.process_batch(d, seg, ids)
+    g = gpu_outputs(e)
+    ref = oracle.Oracle(n, 100, 4096)
+    ref.process(msgs, off)
+    assert_same(g, oracle_outputs(ref))
+
+
+def test_chunk_major_layout_plain_form(eng):
+    """Messages laid out chunk-major ([chunk][book][100]) and processed with one
+    launch per chunk, trades appended: identical to one call per book stream."""
+    n, per, ch = 16, 1000, 100
+    msgs, off = lobgen.generate(lobgen.make_params(78, "three"), [per] * n)
+    cm = np.ascontiguousarray(msgs.reshape(n, per // ch, ch).transpose(1, 0, 2)).reshape(-1)
+    e = eng.Engine(n, 100, 4096, append_trades=True)
+    d = eng.messages_to_device(cm)
+    for c in range(per // ch):
+        seg = torch.arange(0, n * ch + 1, ch, dtype=torch.int64, device="cuda") + c * n * ch
+        e.process_batch(d, seg)
+    ref = oracle.Oracle(n, 100, 4096)
+    ref.process(msgs, off)
+    assert_same(gpu_outputs(e), oracle_outputs(ref))
+
+
+def test_book_subsets_and_empty_segments(eng):
+    n = 40
+    p = lobgen.make_params(9)
+    hs = lobgen.HostStreams(p, n)
+    e = eng.Engine(n, 100, 2048)
+    ref = oracle.Oracle(n, 100, 2048)
+    rng = np.random.default_rng(3)
+    for step in range(6):
+        ids = np.sort(rng.choice(n, size=int(rng.integers(1, n + 1)), replace=False)).astype(np.int32)
+        counts = np.zeros(n, np.int64)
+        counts[ids] = rng.integers(0, 400, size=len(ids))
+        all_m, all_off = hs.advance(counts)
+        seg_counts = counts[ids]
+        seg_m = np.concatenate([all_m[all_off[b]:all_off[b + 1]] for b in ids])
+        seg_off = lobgen.offsets_from_counts(seg_counts)
+        e.process_batch(eng.messages_to_device(seg_m) if len(seg_m) else
+                        torch.zeros((1, 8), dtype=torch.int32, device="cuda"),
+                        torch.from_numpy(seg_off).cuda(), torch.from_numpy(ids).cuda())
+        ref.process(seg_m, seg_off, ids)
+        assert_same(gpu_outputs(e), oracle_outputs(ref))
+
+
+def test_set_book_roundtrip_and_continue(eng):
+    msgs, off = lobgen.generate(lobgen.make_params(21), [3000] * 8)
+    ref = oracle.Oracle(8, 100, 4096)
+    ref.process(msgs, off)
+    bk = ref.book()
+    e = eng.Engine(8, 100, 4096)
+    e.set_book({k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in bk.items()})
+    g = e.book()
+    for k, v in bk.items():
+        assert np.array_equal(g[k].cpu().numpy(), v)
+    more, moff = lobgen.generate(lobgen.make_params(22), [1500] * 8)
+    e.process_batch(eng.messages_to_device(more), torch.from_numpy(moff).cuda())
+    ref2 = oracle.Oracle(8, 100, 4096)
+    ref2.set_book(bk)
+    ref2.process(more, moff)
+    got = gpu_outputs(e)
+    exp = oracle_outputs(ref2)
+    for k in exp:
+        if k != "counters":
+            assert_same({k: got[k]}, {k: exp[k]})
+
+
+def test_bad_book_load_sets_status(eng):
+    e = eng.Engine(2, 8, 16)
+    shp = (2, 2, 8)
+    px = torch.full(shp, -1, dtype=torch.int32, device="cuda")
+    px[0, 0, :3] = torch.tensor([100, 101, 99], dtype=torch.int32)  # bids not descending
+    qty = torch.ones(shp, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros((2, 2), dtype=torch.int32, device="cuda")
+    cnt[0, 0] = 3
+    e.set_book(dict(price=px, qty=qty, oid=qty.clone(), tid=qty.clone(),
+                    time_ns=torch.ones(shp, dtype=torch.int64, device="cuda"), count=cnt))
+    _, st = e.stats()
+    assert int(st.item()) & eng.STATUS_BAD_BOOK_LOAD
+    assert int(e.book()["count"][0, 0].item()) == 0
+
+
+def test_out_of_range_book_id_is_skipped_and_flagged(eng):
+    msgs, off = lobgen.generate(lobgen.make_params(1), [50, 50])
+    e = eng.Engine(4, 100, 64)
+    ids = torch.tensor([1, 7], dtype=torch.int32, device="cuda")
+    e.process_batch(eng.messages_to_device(msgs), torch.from_numpy(off).cuda(), ids)
+    ctr, st = e.stats()
+    assert int(st.item()) & eng.STATUS_BAD_BOOK
+    c = ctr.cpu().numpy()
+    assert c[1, 0] == 50 and c[[0, 2, 3], 0].sum() == 0
+
+
+def test_argument_errors(eng):
+    e = eng.Engine(4, 100, 64)
+    with pytest.raises(eng.LobError):
+        e.set_launch(0, 64)
+    with pytest.raises(eng.LobError):
+        e.set_launch(4, 12)
+    with pytest.raises(eng.LobError):
+        e.levels(65)
+    m = torch.zeros((9, 8), dtype=torch.int32, device="cuda")
+    off = torch.tensor([0, 1, 2], dtype=torch.int64, device="cuda")
+    with pytest.raises(eng.LobError):  # no book ids and n_active != n_books
+        e.process_batch(m, off)
+    with pytest.raises(eng.LobError):  # misaligned messages
+        eng.lob_process_batch(e.h, m.view(-1)[1:], off, torch.tensor([0, 1], dtype=torch.int32,
+                                                                      device="cuda"))
+    with pytest.raises(eng.LobError):
+        eng.Engine(1, 513, 8)
+    with pytest.raises(eng.LobError):
+        eng.Engine(0, 100, 8)
