@@ -1,0 +1,495 @@
+"""Benchmark of the batched order-book engine on one B300 (or N, one rank each).
+
+Default workload: replay_1024x100k -- 1,024 independent books of capacity 100,
+10^5 synthetic messages per book (the config the headline metric is quoted on).
+One step = the whole hot path over the batch: all books from empty through all
+their messages (add / cancel / delete / market matching, trade log written),
+then the top-10 levels of every book.
+
+Forms timed on the same data:
+  persistent  one launch per step: a persistent grid pulls books from a device
+              work queue and keeps each book in shared memory for its whole
+              stream (the reported `value`);
+  plain       one launch per 100-message chunk (1,000 launches per step), book
+              state to and from HBM each launch;
+  plain_graph the plain form's 1,000 launches replayed from a CUDA graph.
+
+`--impl reference` times the CPU oracle (the test-suite's checker, plain C++)
+on the host cores on a bounded sample of the same workload.
+
+Under torchrun every rank runs its own 1,024 books (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("messages/sec (1 B300, bit-exact) batched-persistent vs plain; env steps/sec; "
+          "p50/p99 step ms")
+UNIT = "msgs/s"
+DATA = "synthetic: seeded counter-based order-flow generator standing in for LOBSTER replay data"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="replay_1024x100k")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form legs")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-books", type=int, default=256,
+                    help="books of the CPU-baseline sample (full streams)")
+    ap.add_argument("--launch", default="", help="warps,chunk,ctas_per_sm override")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", "lob_clocks_%d_%d.csv" % (os.getpid(), index))
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def workload_streams(name, rank):
+    import lobgen
+    w = lobgen.WORKLOADS[name]
+    n = w["n_books"]
+    if w.get("msgs"):
+        counts = np.full(n, w["msgs"], np.int64)
+    else:
+        counts = lobgen.lognormal_counts(n, w["seed"])
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    sid = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
+    msgs, off = lobgen.generate(params, counts, stream_ids=sid)
+    return w, params, counts, msgs, off, sid
+
+
+def trade_capacity_for(counts):
+    # enough for every trade of the longest stream (fills/message < 0.7 here)
+    return int(min(1 << 20, max(1024, int(counts.max() * 0.75) + 1024)))
+
+
+# ------------------------------------------------------------------ engine arm
+
+def run_engine(args):
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    from paper_2308_13289_b300 import build as eng_build
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    eng_build.build()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    w, params, counts, msgs, off, sid = workload_streams(args.workload, rank)
+    n = len(counts)
+    total_msgs = int(off[-1])
+    cap = w["capacity"]
+    tcap = trade_capacity_for(counts)
+    depth = 10
+
+    d_msgs = eng.messages_to_device(msgs)
+    d_off = torch.from_numpy(off).cuda()
+    stream = torch.cuda.current_stream()
+
+    # ---------------- persistent form
+    e = eng.Engine(n, cap, tcap)
+    if args.launch:
+        e.set_launch(*[int(x) for x in args.launch.split(",")])
+    lv_out = [torch.empty((n, depth), dtype=torch.int32, device="cuda") for _ in range(4)]
+
+    def step_persistent(ev=None):
+        e.reset()
+        if ev is not None:
+            ev[0].record(stream)
+        e.process_batch(d_msgs, d_off)
+        if ev is not None:
+            ev[1].record(stream)
+        eng.lob_get_levels(e.h, depth, *lv_out)
+
+    for _ in range(args.warmup):
+        step_persistent()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = e.launch_count()
+    torch.cuda.synchronize()
+    barrier()
+    t0.record(stream)
+    for i in range(args.steps):
+        step_persistent(kev[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = e.launch_count() - launches0
+    ms_total = t0.elapsed_time(t1)
+    kernel_ms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+
+    # outputs of the last step for the parity check and the roofline bytes
+    ctr, st = e.stats()
+    trades_per_step = int(ctr[:, 6].sum().item())
+    status = int(st.item())
+
+    # ---------------- plain form: one launch per 100-message chunk
+    plain = plain_graph = None
+    chunk = w.get("chunk", 100)
+    uniform = bool((counts == counts[0]).all()) and counts[0] % chunk == 0
+    if not args.no_plain and uniform:
+        per = int(counts[0])
+        nch = per // chunk
+        cm = torch.empty_like(d_msgs)
+        cm.view(nch, n, chunk, 8).copy_(d_msgs.view(n, nch, chunk, 8).transpose(0, 1))
+        seg = torch.arange(0, n * chunk + 1, chunk, dtype=torch.int64, device="cuda")
+        ep = eng.Engine(n, cap, tcap, append_trades=True)
+        base = cm.data_ptr()
+        rowbytes = n * chunk * 32
+
+        def step_plain():
+            ep.reset()
+            for c in range(nch):
+                rc = eng.lib().lob_process_batch(
+                    ep.h, ctypes.c_void_p(base + c * rowbytes), ctypes.c_void_p(seg.data_ptr()),
+                    None, n, ctypes.c_void_p(stream.cuda_stream))
+                if rc != 0:
+                    raise eng.LobError(rc, "lob_process_batch")
+            eng.lob_get_levels(ep.h, depth, *lv_out)
+
+        plain = time_steps(step_plain, args, stream, barrier, world)
+        plain["launches_per_step"] = nch + 1
+        # same result as the persistent form
+        plain["bit_exact_vs_persistent"] = same_results(e, ep, depth)
+        # graph-captured plain form
+        g = torch.cuda.CUDAGraph()
+        s2 = torch.cuda.Stream()
+        s2.wait_stream(stream)
+        with torch.cuda.stream(s2):
+            step_plain()  # warm the capture stream
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s2):
+                ep.reset()
+                for c in range(nch):
+                    rc = eng.lib().lob_process_batch(
+                        ep.h, ctypes.c_void_p(base + c * rowbytes),
+                        ctypes.c_void_p(seg.data_ptr()), None, n,
+                        ctypes.c_void_p(s2.cuda_stream))
+                    if rc != 0:
+                        raise eng.LobError(rc, "lob_process_batch")
+                eng.lob_get_levels(ep.h, depth, *lv_out, stream=s2)
+        stream.wait_stream(s2)
+        plain_graph = time_steps(lambda: g.replay(), args, stream, barrier, world)
+        plain_graph["launches_per_step"] = nch + 1
+        plain_graph["bit_exact_vs_persistent"] = same_results(e, ep, depth)
+        del g
+        ep.close()
+        del cm
+    clk = clocks.stop()
+
+    # ---------------- end to end through host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        h_msgs = torch.from_numpy(np.ascontiguousarray(msgs).view(np.int32).reshape(-1, 8)).pin_memory()
+        h_off = torch.from_numpy(off).pin_memory()
+        h_lv = [torch.empty((n, depth), dtype=torch.int32).pin_memory() for _ in range(4)]
+        h_cnt = torch.empty(n, dtype=torch.int64).pin_memory()
+        d_cnt = torch.empty(n, dtype=torch.int64, device="cuda")
+
+        def step_e2e():
+            d_msgs.copy_(h_msgs, non_blocking=True)
+            d_off.copy_(h_off, non_blocking=True)
+            e.reset()
+            e.process_batch(d_msgs, d_off)
+            eng.lob_get_levels(e.h, depth, *lv_out)
+            eng.lob_get_trades(e.h, None, d_cnt)
+            for h, d in zip(h_lv, lv_out):
+                h.copy_(d, non_blocking=True)
+            h_cnt.copy_(d_cnt, non_blocking=True)
+
+        r = time_steps(step_e2e, args, stream, barrier, world, steps=max(3, args.steps // 2))
+        e2e = {"value": total_msgs * world / (r["ms_per_step"] / 1e3), "unit": UNIT,
+               "ms_per_step": r["ms_per_step"],
+               "h2d_bytes_per_step": int(h_msgs.numel() * 4 + h_off.numel() * 8),
+               "d2h_bytes_per_step": int(4 * n * depth * 4 + n * 8)}
+
+    # ---------------- parity on a sample of books + CPU baseline (rank 0 only)
+    cpu = parity = None
+    if rank == 0:
+        cpu, parity = cpu_baseline_and_parity(e, msgs, off, counts, cap, tcap, depth,
+                                              args.oracle_books, w)
+
+    # ---------------- roofline of the processing kernel
+    peak, peak_kind = measured_peaks()
+    state_bytes = 2 * n * eng_book_bytes(cap)
+    alg_bytes = 32 * total_msgs + 32 * trades_per_step + state_bytes + 8 * (n + 1)
+    achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 5), "traffic": None, "kernel": "k_process<4>",
+            "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": int(alg_bytes),
+            "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+
+    if rank == 0:
+        value = total_msgs * world / (ms_step / 1e3)
+        line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int32", "data": DATA,
+                "config": {"workload": args.workload, "n_books_per_gpu": n,
+                           "capacity": cap, "messages_per_step_per_gpu": total_msgs,
+                           "trades_per_step_per_gpu": trades_per_step,
+                           "trade_capacity": tcap, "form": "persistent",
+                           "l2": "inputs larger than L2 (%.2f GB of messages)" % (total_msgs * 32 / 1e9),
+                           "seed": w["seed"]},
+                "plain": plain, "plain_graph": plain_graph,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, "parity": parity,
+                "device_status": status}
+        print(json.dumps(line))
+    e.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def eng_book_bytes(cap):
+    k = 1
+    while 32 * k < cap:
+        k *= 2
+    return 48 * 32 * k
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(fn, args, stream, barrier, world, steps=None):
+    import torch
+    steps = steps or args.steps
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(a.elapsed_time(b), world) / steps
+    return {"ms_per_step": round(ms, 4)}
+
+
+def same_results(e1, e2, depth):
+    import torch
+    b1, b2 = e1.book(), e2.book()
+    t1, c1 = e1.trades()
+    t2, c2 = e2.trades()
+    l1, l2 = e1.levels(depth), e2.levels(depth)
+    s1, s2 = e1.stats()[0], e2.stats()[0]
+    ok = all(torch.equal(b1[k], b2[k]) for k in b1) and torch.equal(c1, c2) and \
+        torch.equal(t1, t2) and all(torch.equal(x, y) for x, y in zip(l1, l2)) and \
+        torch.equal(s1, s2)
+    return bool(ok)
+
+
+def cpu_baseline_and_parity(e, msgs, off, counts, cap, tcap, depth, n_sample, w):
+    """Time the CPU oracle (as it stands) on the first `n_sample` books' full
+    streams with all host threads, and compare the GPU's results for those
+    books element by element."""
+    import oracle
+    n_sample = min(n_sample, len(counts))
+    threads = oracle.default_threads()
+    sub_off = off[:n_sample + 1]
+    sub = msgs[:int(sub_off[-1])]
+    o = oracle.Oracle(n_sample, cap, tcap)
+    t = time.perf_counter()
+    o.process(sub, sub_off, threads=threads)
+    dt = time.perf_counter() - t
+    n_msgs = int(sub_off[-1])
+    cpu = {"value": round(n_msgs / dt, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": "first %d of %d books, full %s-message streams (%d messages), "
+                     "std::map oracle, one std::thread per core"
+                     % (n_sample, len(counts), "{:,}".format(int(counts[0])) if
+                        (counts == counts[0]).all() else "lognormal", n_msgs),
+           "seconds": round(dt, 3), "cpu_model": cpu_model()}
+    # parity
+    bk = e.book()
+    gl = e.levels(depth)
+    ctr, _ = e.stats()
+    ok = True
+    ob = o.book()
+    for k, v in ob.items():
+        ok &= np.array_equal(bk[k][:n_sample].cpu().numpy(), v)
+    for gv, ov in zip(gl, o.levels(depth)):
+        ok &= np.array_equal(gv[:n_sample].cpu().numpy(), ov)
+    ok &= np.array_equal(ctr[:n_sample].cpu().numpy(), o.counters())
+    gt, gc = e.trades()
+    ot, oc = o.trades()
+    ok &= np.array_equal(gc[:n_sample].cpu().numpy(), oc)
+    n_cmp = min(n_sample, 32)
+    ok &= np.array_equal(gt[:n_cmp].cpu().numpy(),
+                         ot[:n_cmp].view(np.int32).reshape(n_cmp, tcap, 8))
+    parity = {"books_checked": n_sample, "trade_logs_checked": n_cmp, "bit_exact": bool(ok)}
+    return cpu, parity
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores: each step processes a
+    bounded sample (the first 64 books' full streams) of the same workload."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w, params, counts, msgs, off, sid = workload_streams(args.workload, 0)
+    n_sample = min(64, len(counts))
+    sub_off = off[:n_sample + 1]
+    sub = msgs[:int(sub_off[-1])]
+    cap, tcap = w["capacity"], trade_capacity_for(counts)
+    threads = oracle.default_threads()
+    n_msgs = int(sub_off[-1])
+
+    def step():
+        o = oracle.Oracle(n_sample, cap, tcap)
+        o.process(sub, sub_off, threads=threads)
+        o.levels(10)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t) / args.steps
+    value = n_msgs / dt
+    sample = "first %d of %d books, full streams (%d messages) per step" % (
+        n_sample, len(counts), n_msgs)
+    line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": DATA, "impl": "reference",
+            "config": {"workload": args.workload, "n_books_per_gpu": len(counts),
+                       "capacity": cap, "form": "cpu oracle sample"},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads,
+                             "kind": "oracle", "sample": sample, "cpu_model": cpu_model()},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_engine(args)
+
+
+if __name__ == "__main__":
+    main()
