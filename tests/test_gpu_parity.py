@@ -134,7 +134,8 @@ def test_book_subsets_and_empty_segments(eng):
 
 
 def test_set_book_roundtrip_and_continue(eng):
-    msgs, off = lobgen.generate(lobgen.make_params(21), [3000] * 8)
+    hs = lobgen.HostStreams(lobgen.make_params(21), 8)
+    msgs, off = hs.advance([3000] * 8)
     ref = oracle.Oracle(8, 100, 4096)
     ref.process(msgs, off)
     bk = ref.book()
@@ -143,7 +144,7 @@ def test_set_book_roundtrip_and_continue(eng):
     g = e.book()
     for k, v in bk.items():
         assert np.array_equal(g[k].cpu().numpy(), v)
-    more, moff = lobgen.generate(lobgen.make_params(22), [1500] * 8)
+    more, moff = hs.advance([1500] * 8)
     e.process_batch(eng.messages_to_device(more), torch.from_numpy(moff).cuda())
     ref2 = oracle.Oracle(8, 100, 4096)
     ref2.set_book(bk)
