@@ -210,6 +210,41 @@ int lob_set_book(lob_ctx* ctx, const int32_t* d_price, const int32_t* d_qty,
  * the status word (int32, LOB_STATUS_* bits).  Either pointer may be NULL. */
 int lob_get_stats(lob_ctx* ctx, int64_t* d_counters, int32_t* d_status, void* stream);
 
+/* ------------------------------------------------------ allocation-free call */
+
+/* No counterpart in the paper: an engineering addition for callers that must
+ * not allocate device memory at run time -- for example a service that has
+ * reserved the GPU's memory up front for its own pool, or a latency-critical
+ * loop in which a cudaMalloc/cudaFree would synchronise the device and stall
+ * other streams.  It needs no lob_ctx and allocates nothing: the book state,
+ * per-side counts and work-queue counter it needs live in one fixed 32 MiB
+ * array inside the library (held on every GPU that loads the library, until
+ * the process exits).
+ *
+ * Every one of n_books books starts EMPTY and processes its segment
+ * d_msgs[d_offsets[b] .. d_offsets[b+1]) exactly as lob_process_batch would
+ * (same kernel, same results).  Outputs (caller-owned device memory):
+ *   d_trades       lob_trade_t[n_books][trade_capacity]: trades in execution
+ *                  order; entries past a book's count are left untouched
+ *   d_trade_counts int64[n_books]: trades executed per book
+ *   d_counters     int64[n_books][LOB_N_COUNTERS] (overwritten, not accumulated)
+ *   d_price .. d_count: final canonical book as in lob_get_book (each may be NULL)
+ *   d_status       int32 status word (LOB_STATUS_*), overwritten
+ * Limits: capacity 1..512; the scratch must hold n_books books, about
+ * 32 MiB / (48 * roundup(capacity, 32) + 8) books (5,460 at capacity 100,
+ * 1,365 at capacity 512); larger requests return LOB_E_INVAL with the limit in
+ * lob_last_error().  The first call on a device resolves the array's device
+ * address and sets kernel attributes for that device; make that first call
+ * before any stream capture.  Every call reuses the same array: calls whose
+ * work overlaps on the GPU (different streams, or several host threads) race
+ * and corrupt each other's books; serialise them. */
+int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                               int32_t n_books, int32_t capacity, int32_t trade_capacity,
+                               int32_t overflow_rule, lob_trade_t* d_trades,
+                               int64_t* d_trade_counts, int64_t* d_counters, int32_t* d_price,
+                               int32_t* d_qty, int32_t* d_oid, int32_t* d_tid, int64_t* d_time,
+                               int32_t* d_count, int32_t* d_status, void* stream);
+
 /* ------------------------------------------------------------------ tuning */
 
 /* Launch shape of the processing kernel: warps (= books in flight) per CTA

@@ -129,6 +129,18 @@ def lob_launch_count(h):
     return int(lib().lob_launch_count(h))
 
 
+def lob_process_streams_static(msgs, offsets, n_books, capacity, trade_capacity, overflow_rule,
+                               trades, trade_counts, counters, px=None, qty=None, oid=None,
+                               tid=None, tm=None, count=None, status=None, stream=None):
+    """Allocation-free variant (no context; books start empty; fixed scratch
+    inside the library).  All outputs are caller-owned CUDA tensors."""
+    check(lib().lob_process_streams_static(
+        _ptr(msgs), _ptr(offsets), n_books, capacity, trade_capacity, overflow_rule,
+        _ptr(trades), _ptr(trade_counts), _ptr(counters), _ptr(px), _ptr(qty), _ptr(oid),
+        _ptr(tid), _ptr(tm), _ptr(count), _ptr(status), _stream(stream)),
+        "lob_process_streams_static")
+
+
 # ------------------------------------------------------------------ convenience object
 
 class Engine:

@@ -32,6 +32,7 @@ SIGNATURES = {
     "lob_get_stats": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_set_launch": (ctypes.c_int, [vp, i32, i32, i32]),
     "lob_launch_count": (i64, [vp]),
+    "lob_process_streams_static": (ctypes.c_int, [vp, vp, i32, i32, i32, i32] + [vp] * 10 + [vp]),
     "lob_last_error": (ctypes.c_char_p, []),
     "lob_abi_version": (ctypes.c_int, []),
 }

@@ -12,6 +12,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -757,3 +758,165 @@ int lob_set_launch(lob_ctx* c, int32_t warps_per_cta, int32_t chunk_msgs, int32_
 }
 
 }  // extern "C"
+
+// ------------------------------------------------ allocation-free entry point
+//
+// lob_process_streams_static runs the same processing kernel as
+// lob_process_batch, but takes no context: every book starts empty, and the
+// only device memory it needs besides the caller's inputs and outputs -- the
+// work-queue counter, the per-side order counts and the staged book state --
+// lives in the file-scope array below.  It exists for callers that must not
+// allocate device memory at run time, for example a service that reserved the
+// GPU's memory up front for its own pool, or a latency-critical loop where a
+// cudaMalloc/cudaFree would synchronise the device and stall other streams.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 32u << 20;  // 32 MiB per GPU that loads the library
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+struct StaticSetup {
+    bool done = false;
+    unsigned char* scratch = nullptr;  // device address of g_static_scratch
+    int num_sms = 0;
+    int per_sm[5] = {0, 0, 0, 0, 0};  // resident CTAs of k_process<K>, K = 1,2,4,8,16
+};
+StaticSetup g_static[kMaxDevices];
+std::mutex g_static_mu;
+
+constexpr int kStaticChunk = 64;
+int static_warps(int K) { return K >= 8 ? 4 : 8; }
+int k_index(int K) { return K == 1 ? 0 : K == 2 ? 1 : K == 4 ? 2 : K == 8 ? 3 : 4; }
+
+// Once per device, with that device current: resolve the array's device
+// address and prepare the kernel launch attributes.  Allocates nothing.
+int static_setup(int dev, StaticSetup** out)
+{
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    StaticSetup& s = g_static[dev];
+    if (!s.done) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return lob_cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return lob_cuda_fail(e, "cudaDeviceGetAttribute");
+        const int ks[5] = {1, 2, 4, 8, 16};
+        for (int i = 0; i < 5; ++i) {
+            const int K = ks[i], W = static_warps(K);
+            const int smem = smem_per_warp(K, kStaticChunk) * W;
+            const void* fn = process_kernel(K);
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return lob_cuda_fail(e, "cudaFuncSetAttribute");
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.per_sm[i], fn, 32 * W, smem);
+            if (e != cudaSuccess) return lob_cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+            if (s.per_sm[i] < 1) s.per_sm[i] = 1;
+        }
+        s.scratch = static_cast<unsigned char*>(p);
+        s.done = true;
+    }
+    *out = &s;
+    return LOB_OK;
+}
+
+}  // namespace
+
+extern "C" int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                                          int32_t n_books, int32_t capacity,
+                                          int32_t trade_capacity, int32_t overflow_rule,
+                                          lob_trade_t* d_trades, int64_t* d_trade_counts,
+                                          int64_t* d_counters, int32_t* d_price, int32_t* d_qty,
+                                          int32_t* d_oid, int32_t* d_tid, int64_t* d_time,
+                                          int32_t* d_count, int32_t* d_status, void* stream)
+{
+    if (n_books < 1 || capacity < 1 || capacity > 32 * kMaxK || trade_capacity < 0 ||
+        (overflow_rule != 0 && overflow_rule != 1)) {
+        lob_set_error("lob_process_streams_static: invalid sizes (n_books=%d capacity=%d "
+                      "trade_capacity=%d overflow_rule=%d)",
+                      n_books, capacity, trade_capacity, overflow_rule);
+        return LOB_E_INVAL;
+    }
+    if (!d_msgs || !d_offsets || !d_trade_counts || !d_counters || !d_status ||
+        (trade_capacity > 0 && !d_trades)) {
+        lob_set_error("lob_process_streams_static: null input or output pointer");
+        return LOB_E_INVAL;
+    }
+    if (((uintptr_t)d_msgs & 15u) != 0) {
+        lob_set_error("lob_process_streams_static: messages must be 16-byte aligned");
+        return LOB_E_INVAL;
+    }
+    const int K = k_of(capacity);
+    // scratch layout: [queue: 256 B][counts: n_books*2 int32, 256-aligned][book state]
+    const size_t counts_off = 256;
+    const size_t state_off = counts_off + (((size_t)n_books * 8 + 255) / 256) * 256;
+    const size_t need = state_off + (size_t)n_books * (size_t)lob_book_bytes(K);
+    if (need > kStaticScratchBytes) {
+        lob_set_error("lob_process_streams_static: %d books of capacity %d need %zu bytes of "
+                      "scratch, more than the library's fixed %zu bytes (at most %zu books at "
+                      "this capacity)",
+                      n_books, capacity, need, kStaticScratchBytes,
+                      (kStaticScratchBytes - 512) / ((size_t)lob_book_bytes(K) + 8));
+        return LOB_E_INVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) {
+        lob_set_error("lob_process_streams_static: device index %d not supported", dev);
+        return LOB_E_INVAL;
+    }
+    StaticSetup* s = nullptr;
+    int rc = static_setup(dev, &s);
+    if (rc != LOB_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char* scratch = s->scratch;
+    int32_t* queue = reinterpret_cast<int32_t*>(scratch);
+    int32_t* counts = reinterpret_cast<int32_t*>(scratch + counts_off);
+    char* state = reinterpret_cast<char*>(scratch + state_off);
+    // the array keeps the previous call's contents: clear what must start at zero
+    e = cudaMemsetAsync(queue, 0, 256, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counts, 0, (size_t)n_books * 8, st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d_counters, 0, (size_t)n_books * kNumCtr * sizeof(int64_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_process_streams_static memset");
+
+    ProcArgs a;
+    a.msgs = reinterpret_cast<const Msg*>(d_msgs);
+    a.offsets = d_offsets;
+    a.book_ids = nullptr;
+    a.n_items = n_books;
+    a.n_books = n_books;
+    a.state = state;
+    a.counts = counts;
+    a.trades = reinterpret_cast<Trade*>(d_trades);
+    a.tcounts = d_trade_counts;
+    a.stats = d_counters;
+    a.status = d_status;
+    a.queue = queue;
+    a.cap = capacity;
+    a.rule = overflow_rule;
+    a.trade_cap = trade_capacity;
+    a.append = 0;
+    a.chunk = kStaticChunk;
+    a.pad_ = 0;
+    a.wait_ns = kWaitNs;
+    const int W = static_warps(K);
+    int grid = (n_books + W - 1) / W;
+    const int resident = s->num_sms * s->per_sm[k_index(K)];
+    if (grid > resident) grid = resident;
+    void* args[] = {&a};
+    e = cudaLaunchKernel(process_kernel(K), dim3(grid), dim3(32 * W), args,
+                         (size_t)(smem_per_warp(K, kStaticChunk) * W), st);
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_process_streams_static launch");
+    if (d_price || d_qty || d_oid || d_tid || d_time || d_count) {
+        const int64_t n = (int64_t)n_books * 2 * capacity;
+        dim3 g2((unsigned)((n + 255) / 256)), b2(256);
+        LOB_DISPATCH_K(K, (k_get_book<KK><<<g2, b2, 0, st>>>(state, counts, n_books, capacity,
+                                                             d_price, d_qty, d_oid, d_tid,
+                                                             d_time, d_count)));
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return lob_cuda_fail(e, "lob_process_streams_static dump");
+    }
+    return LOB_OK;
+}
