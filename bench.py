@@ -303,7 +303,7 @@ def run_engine(args):
 
     # ---------------- parity on a sample of books + CPU baseline (rank 0 only)
     cpu = parity = None
-    if rank == 0:
+    if rank == 0 and args.oracle_books > 0:
         cpu, parity = cpu_baseline_and_parity(e, msgs, off, counts, cap, tcap, depth,
                                               args.oracle_books, w)
 

@@ -127,6 +127,10 @@ WORKLOADS = {
     # launches once per 100-message chunk
     "replay_1024x100k": dict(n_books=1024, msgs=100_000, capacity=100, mid_walk="three",
                              seed=20230826, chunk=100),
+    # profiling case: the same books and generator with 10^4 messages per book
+    # (328 MB of messages, still larger than L2)
+    "replay_1024x10k": dict(n_books=1024, msgs=10_000, capacity=100, mid_walk="three",
+                            seed=20230826, chunk=100),
     # 4,096 books, lognormal(ln 1e4, 1.0) counts clipped to [1e3, 2e5], capacity 100
     "uneven_4096_lognormal": dict(n_books=4096, msgs=None, capacity=100, mid_walk="pm1",
                                   seed=20230827),
