@@ -204,30 +204,6 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
     return min(a + b, (uint32_t)kMaxInt);
 }
 
-// ------------------------------------------------------------- one-side views
-
-// Side X: 0 = bids (priority = higher price first), 1 = asks (lower first).
-template <int K, int X>
-struct SideRef {
-    char* base;  // start of this side in shared memory
-    __device__ __forceinline__ int32_t* px() const { return reinterpret_cast<int32_t*>(base + Geo<K>::PX); }
-    __device__ __forceinline__ int32_t* qty() const { return reinterpret_cast<int32_t*>(base + Geo<K>::QTY); }
-    __device__ __forceinline__ int32_t* oid() const { return reinterpret_cast<int32_t*>(base + Geo<K>::OID); }
-    __device__ __forceinline__ int32_t* tid() const { return reinterpret_cast<int32_t*>(base + Geo<K>::TID); }
-    __device__ __forceinline__ int64_t* tm() const { return reinterpret_cast<int64_t*>(base + Geo<K>::TM); }
-    // a resting price `a` ranks at least as well as an incoming price `p`; on
-    // the opposite side of an aggressor this is exactly the crossing test
-    // (Sec. 4.1: buy crosses while P_a >= P_s, sell while P_a <= P_s)
-    static __device__ __forceinline__ bool at_least(int32_t a, int32_t p) { return X == 0 ? a >= p : a <= p; }
-};
-
-// Per-lane counter slot: lane i accumulates counter i of the current book.
-struct Counters {
-    int64_t v;
-    int lane;
-    __device__ __forceinline__ void add(int idx, int64_t x) { v += (lane == idx) ? x : 0; }
-};
-
 // ---------------------------------------------------------------- primitives
 
 // Shift slots [p, n_after) right by one and place `val` at slot p.
@@ -300,31 +276,149 @@ __device__ __forceinline__ bool lane_touches(int lo, int hi)
     return s0 + K > lo && s0 < hi;
 }
 
-// Field-at-a-time versions (keep only one field's vector live).
+// ------------------------------------------------------------ side vectors
+
+// The K slots a lane owns on one side, every field.
+template <int K>
+struct SideVec {
+    int32_t px[K], q[K], oid[K], tid[K];
+    int32_t tlo[K], thi[K];  // time stamp, low and high 32 bits
+};
+
+// v[r] for a run-time r in [0, K) by a tree of selects on the bits of r (a
+// plain indexed read, or a chain of equality selects that the compiler folds
+// back into one, would force the lane's registers into local memory).
 template <int K, typename T>
-__device__ __forceinline__ void field_shift_in(T* arr, int p, int n_after, T val, bool touch)
+__device__ __forceinline__ T pick(const T (&v)[K], int r)
 {
-    T v[K];
-    ld_vec<K>(arr, v);
-    shift_in<K>(v, p, n_after, val);
-    if (touch) st_vec<K>(arr, v);
+    T t[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) t[j] = v[j];
+#pragma unroll
+    for (int w = 1; w < K; w <<= 1) {
+        const bool hi = (r & w) != 0;
+#pragma unroll
+        for (int j = 0; j + w < K; j += 2 * w) t[j] = hi ? t[j + w] : t[j];
+    }
+    return t[0];
 }
 
+// Value of slot s (warp-uniform s) broadcast to every lane.
 template <int K, typename T>
-__device__ __forceinline__ void field_shift_out(T* arr, int p, int n, bool touch)
+__device__ __forceinline__ T slot_value(const T (&v)[K], int s)
 {
-    T v[K];
-    ld_vec<K>(arr, v);
-    shift_out<K>(v, p, n);
-    if (touch) st_vec<K>(arr, v);
+    return __shfl_sync(kFull, pick<K>(v, s % K), s / K);
 }
 
-template <int K, typename T>
-__device__ __forceinline__ void field_drop_front(T* arr, T (&v)[K], int m, bool touch)
+// Side X: 0 = bids (priority = higher price first), 1 = asks (lower first).
+// A resting price `a` ranks at least as well as an incoming price `p`; on the
+// opposite side of an aggressor this is exactly the crossing test (Sec. 4.1:
+// a buy crosses while P_a >= P_s, a sell while P_a <= P_s).
+template <int X>
+__device__ __forceinline__ bool at_least(int32_t a, int32_t p)
 {
-    drop_front<K>(v, m);
-    if (touch) st_vec<K>(arr, v);
+    return X == 0 ? a >= p : a <= p;
 }
+
+// ------------------------------------------------------- storage policies
+//
+// RegBook: both sides stay in registers for a whole message stream (each lane
+// keeps its K slots of every field); used when 2*6*K registers fit (K <= 8).
+// SmemBook: both sides stay in shared memory and each operation moves the
+// lane's slots through registers; used for the largest capacity (K = 16).
+// The book operations below are written once against either policy.
+
+template <int K>
+struct RegBook {
+    SideVec<K> s[2];
+    static constexpr bool kInRegisters = true;
+    // the side itself is modified in place; `tmp` is unused
+    template <int X> __device__ __forceinline__ SideVec<K>& acquire(SideVec<K>&) { return s[X]; }
+    template <int X> __device__ __forceinline__ void release(const SideVec<K>&, bool) {}
+    template <int X> __device__ __forceinline__ int32_t best_px() const
+    {
+        return __shfl_sync(kFull, s[X].px[0], 0);
+    }
+    // qty of slot p held by lane L at position jj
+    template <int X> __device__ __forceinline__ void set_qty(int L, int jj, int p, int32_t q)
+    {
+        const int l = lane_id();
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (l == L && j == jj) s[X].q[j] = q;
+    }
+    // fill from / spill to a staged book image in shared memory
+    __device__ __forceinline__ void from_image(const char* img)
+    {
+        load_side(img, s[0]);
+        load_side(img + Geo<K>::SIDE_BYTES, s[1]);
+    }
+    __device__ __forceinline__ void to_image(char* img) const
+    {
+        store_side(img, s[0]);
+        store_side(img + Geo<K>::SIDE_BYTES, s[1]);
+    }
+    static __device__ __forceinline__ void load_side(const char* b, SideVec<K>& v)
+    {
+        ld_vec<K>(reinterpret_cast<const int32_t*>(b + Geo<K>::PX), v.px);
+        ld_vec<K>(reinterpret_cast<const int32_t*>(b + Geo<K>::QTY), v.q);
+        ld_vec<K>(reinterpret_cast<const int32_t*>(b + Geo<K>::OID), v.oid);
+        ld_vec<K>(reinterpret_cast<const int32_t*>(b + Geo<K>::TID), v.tid);
+        int64_t t[K];
+        ld_vec<K>(reinterpret_cast<const int64_t*>(b + Geo<K>::TM), t);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            v.tlo[j] = (int32_t)(uint32_t)(uint64_t)t[j];
+            v.thi[j] = (int32_t)(uint32_t)((uint64_t)t[j] >> 32);
+        }
+    }
+    static __device__ __forceinline__ void store_side(char* b, const SideVec<K>& v)
+    {
+        st_vec<K>(reinterpret_cast<int32_t*>(b + Geo<K>::PX), v.px);
+        st_vec<K>(reinterpret_cast<int32_t*>(b + Geo<K>::QTY), v.q);
+        st_vec<K>(reinterpret_cast<int32_t*>(b + Geo<K>::OID), v.oid);
+        st_vec<K>(reinterpret_cast<int32_t*>(b + Geo<K>::TID), v.tid);
+        int64_t t[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            t[j] = (int64_t)(((uint64_t)(uint32_t)v.thi[j] << 32) | (uint32_t)v.tlo[j]);
+        st_vec<K>(reinterpret_cast<int64_t*>(b + Geo<K>::TM), t);
+    }
+};
+
+template <int K>
+struct SmemBook {
+    char* base;  // staged book image in shared memory
+    static constexpr bool kInRegisters = false;
+    template <int X> __device__ __forceinline__ char* side() const { return base + X * Geo<K>::SIDE_BYTES; }
+    // the lane's slots are moved through `tmp` and written back on release
+    template <int X> __device__ __forceinline__ SideVec<K>& acquire(SideVec<K>& tmp)
+    {
+        RegBook<K>::load_side(side<X>(), tmp);
+        return tmp;
+    }
+    template <int X> __device__ __forceinline__ void release(const SideVec<K>& v, bool touch)
+    {
+        if (touch) RegBook<K>::store_side(side<X>(), v);
+    }
+    template <int X> __device__ __forceinline__ int32_t best_px() const
+    {
+        return reinterpret_cast<const int32_t*>(side<X>() + Geo<K>::PX)[0];
+    }
+    template <int X> __device__ __forceinline__ void set_qty(int L, int, int p, int32_t q)
+    {
+        if (lane_id() == L) reinterpret_cast<int32_t*>(side<X>() + Geo<K>::QTY)[p] = q;
+    }
+    __device__ __forceinline__ void from_image(const char*) {}
+    __device__ __forceinline__ void to_image(char*) const {}
+};
+
+// Per-lane counter slot: lane i accumulates counter i of the current book.
+struct Counters {
+    int64_t v;
+    int lane;
+    __device__ __forceinline__ void add(int idx, int64_t x) { v += (lane == idx) ? x : 0; }
+};
 
 // ------------------------------------------------------------ book operations
 
@@ -333,21 +427,17 @@ __device__ __forceinline__ void field_drop_front(T* arr, T (&v)[K], int m, bool 
 // when the side already holds `cap` orders the worst one is evicted if the new
 // order's price is strictly better than its price, else the rest is rejected
 // (rule 1: always rejected).
-template <int K, int X>
-__device__ __forceinline__ void add_order(SideRef<K, X> sd, int& n, int cap, int rule, int32_t P,
-                                          int32_t Q, int32_t oid, int32_t tid, int64_t tm,
-                                          Counters& ctr)
+template <int K, int X, class Book>
+__device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, int32_t P, int32_t Q,
+                                          int32_t oid, int32_t tid, int64_t tm, Counters& ctr)
 {
     const int l = lane_id();
-    int32_t vpx[K];
-    ld_vec<K>(sd.px(), vpx);
+    SideVec<K> tmp;
+    SideVec<K>& v = bk.template acquire<X>(tmp);
     // insertion point: number of resting orders with a price at least as good
     unsigned cnt = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const int s = l * K + j;
-        cnt += (s < n && SideRef<K, X>::at_least(vpx[j], P)) ? 1u : 0u;
-    }
+    for (int j = 0; j < K; ++j) cnt += (l * K + j < n && at_least<X>(v.px[j], P)) ? 1u : 0u;
     const int p = (int)__reduce_add_sync(kFull, cnt);
     int n_after = n + 1;
     if (n >= cap) {
@@ -357,58 +447,54 @@ __device__ __forceinline__ void add_order(SideRef<K, X> sd, int& n, int cap, int
             return;
         }
         // the worst order (slot cap-1) has a strictly worse price: evict it
-        const int32_t qe = sd.qty()[cap - 1];
         ctr.add(CTR_EVICTED, 1);
-        ctr.add(CTR_EVICTED_QTY, qe);
+        ctr.add(CTR_EVICTED_QTY, slot_value<K>(v.q, cap - 1));
         n_after = cap;
     }
-    const bool touch = lane_touches<K>(p, n_after);
-    shift_in<K>(vpx, p, n_after, P);
-    if (touch) st_vec<K>(sd.px(), vpx);
-    field_shift_in<K>(sd.qty(), p, n_after, Q, touch);
-    field_shift_in<K>(sd.oid(), p, n_after, oid, touch);
-    field_shift_in<K>(sd.tid(), p, n_after, tid, touch);
-    field_shift_in<K>(sd.tm(), p, n_after, tm, touch);
+    shift_in<K>(v.px, p, n_after, P);
+    shift_in<K>(v.q, p, n_after, Q);
+    shift_in<K>(v.oid, p, n_after, oid);
+    shift_in<K>(v.tid, p, n_after, tid);
+    shift_in<K>(v.tlo, p, n_after, (int32_t)(uint32_t)(uint64_t)tm);
+    shift_in<K>(v.thi, p, n_after, (int32_t)(uint32_t)((uint64_t)tm >> 32));
+    bk.template release<X>(v, lane_touches<K>(p, n_after));
     n = n_after;
     ctr.add(CTR_RESTED, 1);
 }
 
 // Cancellation (Sec. 4.1 item 2): locate OID on side X and remove Q from it;
 // the order leaves the book when its quantity drops to 0 or below.
-template <int K, int X>
-__device__ __forceinline__ void cancel_order(SideRef<K, X> sd, int& n, int32_t oid, int32_t Q,
-                                             Counters& ctr)
+template <int K, int X, class Book>
+__device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int32_t Q, Counters& ctr)
 {
     const int l = lane_id();
-    int32_t vo[K];
-    ld_vec<K>(sd.oid(), vo);
+    SideVec<K> tmp;
+    SideVec<K>& v = bk.template acquire<X>(tmp);
     int jj = -1;
 #pragma unroll
     for (int j = K - 1; j >= 0; --j)
-        if (l * K + j < n && vo[j] == oid) jj = j;
+        if (l * K + j < n && v.oid[j] == oid) jj = j;
     const unsigned hit = __ballot_sync(kFull, jj >= 0);
-    if (hit == 0) {
-        ctr.add(CTR_CANCEL_MISS, 1);
-        return;
-    }
+    if (hit == 0) return;  // not live on this side: no-op (counted at the end)
     ctr.add(CTR_CANCEL_HIT, 1);
     const int L = __ffs(hit) - 1;
-    const int p = L * K + __shfl_sync(kFull, jj, L);
-    const int32_t q_old = sd.qty()[p];
+    const int j_hit = __shfl_sync(kFull, jj, L);
+    const int p = L * K + j_hit;
+    const int32_t q_old = __shfl_sync(kFull, pick<K>(v.q, j_hit), L);
     const int32_t q_new = q_old - Q;
     if (q_new > 0) {
-        if (l == L) sd.qty()[p] = q_new;
+        bk.template set_qty<X>(L, j_hit, p, q_new);
         ctr.add(CTR_CANCELLED_QTY, Q);
         return;
     }
     ctr.add(CTR_CANCELLED_QTY, q_old);
-    const bool touch = lane_touches<K>(p, n - 1);
-    shift_out<K>(vo, p, n);
-    if (touch) st_vec<K>(sd.oid(), vo);
-    field_shift_out<K>(sd.px(), p, n, touch);
-    field_shift_out<K>(sd.qty(), p, n, touch);
-    field_shift_out<K>(sd.tid(), p, n, touch);
-    field_shift_out<K>(sd.tm(), p, n, touch);
+    shift_out<K>(v.px, p, n);
+    shift_out<K>(v.q, p, n);
+    shift_out<K>(v.oid, p, n);
+    shift_out<K>(v.tid, p, n);
+    shift_out<K>(v.tlo, p, n);
+    shift_out<K>(v.thi, p, n);
+    bk.template release<X>(v, lane_touches<K>(p, n - 1));
     n -= 1;
 }
 
@@ -427,24 +513,22 @@ struct TradeSink {
 // slot s therefore receives min(Q_s, max(0, Q - (quantity of slots before s))),
 // which one saturating warp prefix scan gives for all slots at once.
 // Returns the aggressor's remaining quantity max(0, Q_a).
-template <int K, int Y>
-__device__ __forceinline__ int32_t match_order(SideRef<K, Y> sd, int& n, int32_t P, int32_t Q,
-                                               int32_t oid_a, int32_t tid_a, int64_t tm_a,
-                                               TradeSink& ts, Counters& ctr)
+template <int K, int Y, class Book>
+__device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int32_t Q, int32_t oid_a,
+                                               int32_t tid_a, int64_t tm_a, TradeSink& ts,
+                                               Counters& ctr)
 {
     const int l = lane_id();
-    int32_t vpx[K], vq[K];
-    ld_vec<K>(sd.px(), vpx);
-    ld_vec<K>(sd.qty(), vq);
+    SideVec<K> tmp;
+    SideVec<K>& v = bk.template acquire<Y>(tmp);
 
     // crossing quantity per slot and lane-local inclusive prefix
     uint32_t cq[K], loc[K];
     uint32_t acc = 0;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const int s = l * K + j;
-        const bool c = s < n && SideRef<K, Y>::at_least(vpx[j], P);
-        cq[j] = c ? (uint32_t)vq[j] : 0u;
+        const bool c = l * K + j < n && at_least<Y>(v.px[j], P);
+        cq[j] = c ? (uint32_t)v.q[j] : 0u;
         acc = sat_add(acc, cq[j]);
         loc[j] = acc;
     }
@@ -476,19 +560,15 @@ __device__ __forceinline__ int32_t match_order(SideRef<K, Y> sd, int& n, int32_t
     const int32_t F = (int32_t)min(total, (uint32_t)Q);    // quantity traded
 
     // trades: the filled slots are the prefix [0, nf), trade k -> slot k
-    int32_t vo[K], vt[K];
-    ld_vec<K>(sd.oid(), vo);
-    ld_vec<K>(sd.tid(), vt);
     const int32_t tlo = (int32_t)(uint32_t)(uint64_t)tm_a;
     const int32_t thi = (int32_t)(uint32_t)((uint64_t)tm_a >> 32);
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const int s = l * K + j;
-        const int64_t idx = ts.count + s;
+        const int64_t idx = ts.count + l * K + j;
         if (fill[j] > 0 && idx < ts.cap) {
             int4* dst = reinterpret_cast<int4*>(ts.log + idx);
-            dst[0] = make_int4(vpx[j], fill[j], oid_a, vo[j]);
-            dst[1] = make_int4(tid_a, vt[j], tlo, thi);
+            dst[0] = make_int4(v.px[j], fill[j], oid_a, v.oid[j]);
+            dst[1] = make_int4(tid_a, v.tid[j], tlo, thi);
         }
     }
     const int64_t stored_before = min(ts.count, (int64_t)ts.cap);
@@ -501,79 +581,100 @@ __device__ __forceinline__ int32_t match_order(SideRef<K, Y> sd, int& n, int32_t
     // standing quantities after the fills (Q_s' per slot), then drop the m
     // fully filled orders at the front (Q <= 0 cleanup)
 #pragma unroll
-    for (int j = 0; j < K; ++j) vq[j] -= fill[j];
-    const int n_old = n;
+    for (int j = 0; j < K; ++j) v.q[j] -= fill[j];
     if (m > 0) {
-        const bool touch = lane_touches<K>(0, n_old - m);
-        field_drop_front<K>(sd.px(), vpx, m, touch);
-        field_drop_front<K>(sd.qty(), vq, m, touch);
-        field_drop_front<K>(sd.oid(), vo, m, touch);
-        field_drop_front<K>(sd.tid(), vt, m, touch);
-        int64_t vtm[K];
-        ld_vec<K>(sd.tm(), vtm);
-        field_drop_front<K>(sd.tm(), vtm, m, touch);
-        n = n_old - m;
+        drop_front<K>(v.px, m);
+        drop_front<K>(v.q, m);
+        drop_front<K>(v.oid, m);
+        drop_front<K>(v.tid, m);
+        drop_front<K>(v.tlo, m);
+        drop_front<K>(v.thi, m);
+        bk.template release<Y>(v, lane_touches<K>(0, n - m));
+        n -= m;
     } else if (nf > 0) {
         // only slot 0 was partly filled
-        if (l == 0) sd.qty()[0] = vq[0];
+        bk.template set_qty<Y>(0, 0, 0, v.q[0]);
     }
     return Q - F;
 }
 
-// Message dispatch (Sec. 4.2).  `book` points at the book in shared memory,
-// n[0] / n[1] are the bid / ask counts (warp-uniform).
-template <int K>
-__device__ __forceinline__ void process_message(char* book, int& n_bid, int& n_ask, int cap,
-                                                int rule, const Msg& m, TradeSink& ts,
-                                                Counters& ctr)
+// Dispatch codes written by the chunk pre-pass (Sec. 4.2: eight type x side
+// cases, padding and malformed messages folded into one "skip" code).
+enum : int32_t {
+    OP_SKIP = 0, OP_LIMIT_BID, OP_LIMIT_ASK, OP_CANCEL_BID, OP_CANCEL_ASK, OP_MARKET_BID,
+    OP_MARKET_ASK
+};
+
+// Classify one message (the part of Sec. 4.2 that does not depend on the book):
+// returns the dispatch code; malformed messages (type outside 0..4, side not
+// +-1, Q <= 0, limit price <= 0) and type-0 padding map to OP_SKIP.
+__device__ __forceinline__ int32_t classify(int32_t T, int32_t S, int32_t P, int32_t Q, int& counter)
 {
-    SideRef<K, 0> bids{book};
-    SideRef<K, 1> asks{book + Geo<K>::SIDE_BYTES};
-    const int32_t T = m.type;
     if (T == 0) {
-        ctr.add(CTR_NOOP, 1);
-        return;
+        counter = CTR_NOOP;
+        return OP_SKIP;
     }
-    if (T < 0 || T > 4 || (m.side != 1 && m.side != -1) || m.qty <= 0 ||
-        (T == 1 && m.price <= 0)) {
-        ctr.add(CTR_INVALID, 1);
-        return;
+    if (T < 0 || T > 4 || (S != 1 && S != -1) || Q <= 0 || (T == 1 && P <= 0)) {
+        counter = CTR_INVALID;
+        return OP_SKIP;
     }
-    if (T == 1) {  // limit: match against the opposite side, then rest the remainder
-        ctr.add(CTR_LIMIT, 1);
-        ctr.add(CTR_LIMIT_QTY, m.qty);
-        int32_t rest = m.qty;
-        if (m.side == 1) {
-            if (n_ask > 0 && SideRef<K, 1>::at_least(asks.px()[0], m.price))
-                rest = match_order<K, 1>(asks, n_ask, m.price, rest, m.oid, m.tid, m.time_ns, ts, ctr);
-            if (rest > 0)
-                add_order<K, 0>(bids, n_bid, cap, rule, m.price, rest, m.oid, m.tid, m.time_ns, ctr);
-        } else {
-            if (n_bid > 0 && SideRef<K, 0>::at_least(bids.px()[0], m.price))
-                rest = match_order<K, 0>(bids, n_bid, m.price, rest, m.oid, m.tid, m.time_ns, ts, ctr);
-            if (rest > 0)
-                add_order<K, 1>(asks, n_ask, cap, rule, m.price, rest, m.oid, m.tid, m.time_ns, ctr);
-        }
-    } else if (T == 4) {  // market: price 0 (sell) / max_int (buy), remainder dropped
-        ctr.add(CTR_MARKET, 1);
-        ctr.add(CTR_MARKET_QTY, m.qty);
-        int32_t rest = m.qty;
-        if (m.side == 1) {
-            if (n_ask > 0)
-                rest = match_order<K, 1>(asks, n_ask, kMaxInt, rest, m.oid, m.tid, m.time_ns, ts, ctr);
-        } else {
-            if (n_bid > 0)
-                rest = match_order<K, 0>(bids, n_bid, 0, rest, m.oid, m.tid, m.time_ns, ts, ctr);
-        }
+    const int bid = S == 1 ? 0 : 1;
+    if (T == 1) {
+        counter = CTR_LIMIT;
+        return OP_LIMIT_BID + bid;
+    }
+    if (T == 4) {
+        counter = CTR_MARKET;
+        return OP_MARKET_BID + bid;
+    }
+    counter = CTR_CANCEL;
+    return OP_CANCEL_BID + bid;
+}
+
+// Apply one classified message to the book (Sec. 4.2 dispatch; n_bid / n_ask
+// are the warp-uniform side counts).
+template <int K, class Book>
+__device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, int cap, int rule,
+                                              int32_t op, int32_t P, int32_t Q, int32_t oid,
+                                              int32_t tid, int64_t tm, TradeSink& ts, Counters& ctr)
+{
+    switch (op) {
+    case OP_LIMIT_BID: {  // buy limit: match the asks, then rest the remainder as a bid
+        int32_t rest = Q;
+        if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), P))
+            rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tm, ts, ctr);
+        if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tm, ctr);
+        break;
+    }
+    case OP_LIMIT_ASK: {
+        int32_t rest = Q;
+        if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), P))
+            rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tm, ts, ctr);
+        if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tm, ctr);
+        break;
+    }
+    case OP_MARKET_BID: {  // market buy: price max_int, remainder dropped
+        int32_t rest = Q;
+        if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tm, ts, ctr);
         ctr.add(CTR_MARKET_DISCARDED_QTY, rest);
-    } else {  // cancel and delete are treated identically
-        ctr.add(CTR_CANCEL, 1);
-        if (m.side == 1)
-            cancel_order<K, 0>(bids, n_bid, m.oid, m.qty, ctr);
-        else
-            cancel_order<K, 1>(asks, n_ask, m.oid, m.qty, ctr);
+        break;
     }
-    __syncwarp();
+    case OP_MARKET_ASK: {  // market sell: price 0
+        int32_t rest = Q;
+        if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tm, ts, ctr);
+        ctr.add(CTR_MARKET_DISCARDED_QTY, rest);
+        break;
+    }
+    case OP_CANCEL_BID:  // cancel and delete are treated identically
+        cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
+        break;
+    case OP_CANCEL_ASK:
+        cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
+        break;
+    default:
+        break;
+    }
+    if constexpr (!Book::kInRegisters) __syncwarp();
 }
 
 }  // namespace lob

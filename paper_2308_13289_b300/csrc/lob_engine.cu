@@ -77,29 +77,37 @@ __host__ __device__ constexpr int warp_smem_bytes(int chunk)
 
 // threads per CTA the processing kernel is compiled for (bounds registers)
 template <int K>
-constexpr int max_threads() { return K >= 8 ? 256 : 512; }
+constexpr int max_threads() { return K >= 4 ? 256 : 512; }
 
-__device__ __forceinline__ Msg load_msg(const Msg* p)
+// Books whose two sides fit in registers (2 sides x 6 words x K per lane) stay
+// there for the whole stream; the largest capacity works in shared memory.
+template <int K>
+struct BookPolicy {
+    using type = RegBook<K>;
+};
+template <>
+struct BookPolicy<16> {
+    using type = SmemBook<16>;
+};
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t x)
 {
-    const int4* q = reinterpret_cast<const int4*>(p);
-    int4 a = q[0], b = q[1];
-    Msg m;
-    m.type = a.x; m.side = a.y; m.price = a.z; m.qty = a.w;
-    m.oid = b.x; m.tid = b.y;
-    m.time_ns = (int64_t)(((uint64_t)(uint32_t)b.w << 32) | (uint32_t)b.z);
-    return m;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    return x;
 }
 
 template <int K>
-__global__ void __launch_bounds__(max_threads<K>()) k_process(ProcArgs a)
+__global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
 {
+    using Book = typename BookPolicy<K>::type;
     extern __shared__ __align__(128) char smem[];
     const int l = lane_id();
     const int warp = threadIdx.x >> 5;
     const int W = blockDim.x >> 5;
     const int chunk = a.chunk;
     char* base = smem + warp * warp_smem_bytes<K>(chunk);
-    char* book = base;
+    char* image = base;  // staged book image (the whole book for the shared-memory policy)
     char* msgbuf = base + Geo<K>::BOOK_BYTES;
     uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk * 32);
     const int total_warps = gridDim.x * W;
@@ -146,12 +154,17 @@ __global__ void __launch_bounds__(max_threads<K>()) k_process(ProcArgs a)
                 const int64_t c0 = lo + (int64_t)c * chunk;
                 const uint32_t cnt = (uint32_t)min((int64_t)chunk, hi - c0);
                 mbar_expect_tx(&bar[st], cnt * 32 + (c == 0 ? Geo<K>::BOOK_BYTES : 0));
-                if (c == 0) bulk_g2s(book, gbook, Geo<K>::BOOK_BYTES, &bar[st]);
+                if (c == 0) bulk_g2s(image, gbook, Geo<K>::BOOK_BYTES, &bar[st]);
                 bulk_g2s(msgbuf + st * chunk * 32, a.msgs + c0, cnt * 32, &bar[st]);
             }
         }
         int n_bid = a.counts[2 * b], n_ask = a.counts[2 * b + 1];
         Counters ctr{0, l};
+        Book bk;
+        if constexpr (!Book::kInRegisters) bk.base = image;
+        // book-independent counters, accumulated by the pre-pass per lane
+        int32_t c_kind[5] = {0, 0, 0, 0, 0};  // noop, invalid, limit, cancel, market
+        int64_t q_limit = 0, q_market = 0;
         for (int c = 0; c < nchunks; ++c) {
             const uint32_t st = (g + c) & 1, par = ((g + c) >> 1) & 1;
             if (!mbar_wait_bounded(&bar[st], par, a.wait_ns)) {
@@ -163,11 +176,37 @@ __global__ void __launch_bounds__(max_threads<K>()) k_process(ProcArgs a)
                 failed = true;
                 break;
             }
-            const Msg* mb = reinterpret_cast<const Msg*>(msgbuf + st * chunk * 32);
+            if (c == 0) bk.from_image(image);
+            int4* mb = reinterpret_cast<int4*>(msgbuf + st * chunk * 32);
             const int cnt = (int)min((int64_t)chunk, hi - (lo + (int64_t)c * chunk));
+            // pre-pass, 32 messages at a time: validate and classify (the part of
+            // Sec. 4.2 that does not depend on the book); the dispatch code
+            // replaces the type word in the staged copy
+            for (int i = l; i < cnt; i += 32) {
+                const int4 h = mb[2 * i];
+                int kind = 0;
+                const int32_t op = classify(h.x, h.y, h.z, h.w, kind);
+                mb[2 * i].x = op;
+                c_kind[0] += kind == CTR_NOOP;
+                c_kind[1] += kind == CTR_INVALID;
+                c_kind[2] += kind == CTR_LIMIT;
+                c_kind[3] += kind == CTR_CANCEL;
+                c_kind[4] += kind == CTR_MARKET;
+                q_limit += kind == CTR_LIMIT ? h.w : 0;
+                q_market += kind == CTR_MARKET ? h.w : 0;
+            }
+            __syncwarp();
+            // the book-dependent part, strictly in order
+            int4 na = mb[0], nb = mb[1];
             for (int i = 0; i < cnt; ++i) {
-                const Msg m = load_msg(mb + i);
-                process_message<K>(book, n_bid, n_ask, a.cap, a.rule, m, ts, ctr);
+                const int4 ha = na, hb = nb;
+                if (i + 1 < cnt) {
+                    na = mb[2 * i + 2];
+                    nb = mb[2 * i + 3];
+                }
+                const int64_t tm = (int64_t)(((uint64_t)(uint32_t)hb.w << 32) | (uint32_t)hb.z);
+                apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
+                                 tm, ts, ctr);
             }
             __syncwarp();
             if (c + 2 < nchunks && l == 0) {
@@ -181,11 +220,24 @@ __global__ void __launch_bounds__(max_threads<K>()) k_process(ProcArgs a)
         if (failed) break;
         g += (uint32_t)nchunks;
         // write the book back
-        const int4* src = reinterpret_cast<const int4*>(book);
+        bk.to_image(image);
+        __syncwarp();
+        const int4* src = reinterpret_cast<const int4*>(image);
         int4* dst = reinterpret_cast<int4*>(gbook);
 #pragma unroll 4
         for (int i = l; i < Geo<K>::BOOK_BYTES / 16; i += 32) dst[i] = src[i];
         ctr.add(CTR_MSGS, nmsg);
+        ctr.add(CTR_NOOP, __reduce_add_sync(kFull, (unsigned)c_kind[0]));
+        ctr.add(CTR_INVALID, __reduce_add_sync(kFull, (unsigned)c_kind[1]));
+        ctr.add(CTR_LIMIT, __reduce_add_sync(kFull, (unsigned)c_kind[2]));
+        ctr.add(CTR_CANCEL, __reduce_add_sync(kFull, (unsigned)c_kind[3]));
+        ctr.add(CTR_MARKET, __reduce_add_sync(kFull, (unsigned)c_kind[4]));
+        ctr.add(CTR_LIMIT_QTY, warp_sum64(q_limit));
+        ctr.add(CTR_MARKET_QTY, warp_sum64(q_market));
+        // a cancel that found no live order is a miss
+        const int64_t n_cancel = __shfl_sync(kFull, ctr.v, CTR_CANCEL);
+        const int64_t n_hit = __shfl_sync(kFull, ctr.v, CTR_CANCEL_HIT);
+        ctr.add(CTR_CANCEL_MISS, n_cancel - n_hit);
         if (l < kNumCtr) a.stats[(int64_t)b * kNumCtr + l] += ctr.v;
         if (l == 0) {
             a.counts[2 * b] = n_bid;
@@ -381,7 +433,7 @@ int smem_per_warp(int K, int chunk)
     }
 }
 
-int max_warps(int K) { return K >= 8 ? 8 : 16; }
+int max_warps(int K) { return K >= 4 ? 8 : 16; }
 
 }  // namespace
 
@@ -533,7 +585,7 @@ int lob_create(lob_ctx** out, const lob_config_t* cfg, void* stream)
         lob_destroy(c);
         return lob_cuda_fail(e, "lob_create memset");
     }
-    int rc = configure_launch(c, c->K >= 8 ? 4 : 8, 64, 0);
+    int rc = configure_launch(c, 4, 64, 0);
     if (rc != LOB_OK) {
         lob_destroy(c);
         return rc;
