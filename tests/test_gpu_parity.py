@@ -61,7 +61,7 @@ def test_small_workload_reject_rule(eng):
     assert_same(g, r)
 
 
-@pytest.mark.parametrize("launch", [(1, 8, 0), (4, 64, 0), (16, 64, 0), (2, 1024, 1), (3, 40, 2)])
+@pytest.mark.parametrize("launch", [(1, 8, 0), (4, 64, 0), (8, 64, 0), (2, 1024, 1), (3, 40, 2)])
 def test_launch_shapes(eng, launch):
     w = lobgen.WORKLOADS["small_16x10k"]
     msgs, off = lobgen.generate(lobgen.make_params(w["seed"], w["mid_walk"]), [w["msgs"]] * 16)
