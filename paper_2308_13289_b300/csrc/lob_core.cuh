@@ -420,6 +420,15 @@ struct Counters {
     __device__ __forceinline__ void add(int idx, int64_t x) { v += (lane == idx) ? x : 0; }
 };
 
+// Book-dependent counters of the current work item, kept warp-uniform (every
+// lane holds the same value) and folded into Counters once per item.  Trade
+// counts are not tallied: they follow from the trade-log position.
+struct Tally {
+    int32_t rested = 0, rejected = 0, evicted = 0, cancel_hit = 0;
+    int64_t rejected_qty = 0, evicted_qty = 0, cancelled_qty = 0, traded_qty = 0,
+            discarded_qty = 0;
+};
+
 // ------------------------------------------------------------ book operations
 
 // Add the remaining quantity Q as one new order (Sec. 4.1 item 1, Sec. 4.2
@@ -429,7 +438,8 @@ struct Counters {
 // (rule 1: always rejected).
 template <int K, int X, class Book>
 __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, int32_t P, int32_t Q,
-                                          int32_t oid, int32_t tid, int64_t tm, Counters& ctr)
+                                          int32_t oid, int32_t tid, int32_t tlo, int32_t thi,
+                                          Tally& ctr)
 {
     const int l = lane_id();
     SideVec<K> tmp;
@@ -442,30 +452,30 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
     int n_after = n + 1;
     if (n >= cap) {
         if (rule != 0 || p >= cap) {
-            ctr.add(CTR_REJECTED, 1);
-            ctr.add(CTR_REJECTED_QTY, Q);
+            ctr.rejected += 1;
+            ctr.rejected_qty += Q;
             return;
         }
         // the worst order (slot cap-1) has a strictly worse price: evict it
-        ctr.add(CTR_EVICTED, 1);
-        ctr.add(CTR_EVICTED_QTY, slot_value<K>(v.q, cap - 1));
+        ctr.evicted += 1;
+        ctr.evicted_qty += slot_value<K>(v.q, cap - 1);
         n_after = cap;
     }
     shift_in<K>(v.px, p, n_after, P);
     shift_in<K>(v.q, p, n_after, Q);
     shift_in<K>(v.oid, p, n_after, oid);
     shift_in<K>(v.tid, p, n_after, tid);
-    shift_in<K>(v.tlo, p, n_after, (int32_t)(uint32_t)(uint64_t)tm);
-    shift_in<K>(v.thi, p, n_after, (int32_t)(uint32_t)((uint64_t)tm >> 32));
+    shift_in<K>(v.tlo, p, n_after, tlo);
+    shift_in<K>(v.thi, p, n_after, thi);
     bk.template release<X>(v, lane_touches<K>(p, n_after));
     n = n_after;
-    ctr.add(CTR_RESTED, 1);
+    ctr.rested += 1;
 }
 
 // Cancellation (Sec. 4.1 item 2): locate OID on side X and remove Q from it;
 // the order leaves the book when its quantity drops to 0 or below.
 template <int K, int X, class Book>
-__device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int32_t Q, Counters& ctr)
+__device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int32_t Q, Tally& ctr)
 {
     const int l = lane_id();
     SideVec<K> tmp;
@@ -476,7 +486,7 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
         if (l * K + j < n && v.oid[j] == oid) jj = j;
     const unsigned hit = __ballot_sync(kFull, jj >= 0);
     if (hit == 0) return;  // not live on this side: no-op (counted at the end)
-    ctr.add(CTR_CANCEL_HIT, 1);
+    ctr.cancel_hit += 1;
     const int L = __ffs(hit) - 1;
     const int j_hit = __shfl_sync(kFull, jj, L);
     const int p = L * K + j_hit;
@@ -484,10 +494,10 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
     const int32_t q_new = q_old - Q;
     if (q_new > 0) {
         bk.template set_qty<X>(L, j_hit, p, q_new);
-        ctr.add(CTR_CANCELLED_QTY, Q);
+        ctr.cancelled_qty += Q;
         return;
     }
-    ctr.add(CTR_CANCELLED_QTY, q_old);
+    ctr.cancelled_qty += q_old;
     shift_out<K>(v.px, p, n);
     shift_out<K>(v.q, p, n);
     shift_out<K>(v.oid, p, n);
@@ -515,8 +525,8 @@ struct TradeSink {
 // Returns the aggressor's remaining quantity max(0, Q_a).
 template <int K, int Y, class Book>
 __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int32_t Q, int32_t oid_a,
-                                               int32_t tid_a, int64_t tm_a, TradeSink& ts,
-                                               Counters& ctr)
+                                               int32_t tid_a, int32_t tlo, int32_t thi,
+                                               TradeSink& ts, Tally& ctr)
 {
     const int l = lane_id();
     SideVec<K> tmp;
@@ -560,8 +570,6 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
     const int32_t F = (int32_t)min(total, (uint32_t)Q);    // quantity traded
 
     // trades: the filled slots are the prefix [0, nf), trade k -> slot k
-    const int32_t tlo = (int32_t)(uint32_t)(uint64_t)tm_a;
-    const int32_t thi = (int32_t)(uint32_t)((uint64_t)tm_a >> 32);
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int64_t idx = ts.count + l * K + j;
@@ -571,12 +579,8 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
             dst[1] = make_int4(tid_a, v.tid[j], tlo, thi);
         }
     }
-    const int64_t stored_before = min(ts.count, (int64_t)ts.cap);
-    const int64_t stored_after = min(ts.count + nf, (int64_t)ts.cap);
-    ctr.add(CTR_TRADES_DROPPED, nf - (stored_after - stored_before));
     ts.count += nf;
-    ctr.add(CTR_TRADES, nf);
-    ctr.add(CTR_TRADED_QTY, F);
+    ctr.traded_qty += F;
 
     // standing quantities after the fills (Q_s' per slot), then drop the m
     // fully filled orders at the front (Q <= 0 cleanup)
@@ -632,47 +636,35 @@ __device__ __forceinline__ int32_t classify(int32_t T, int32_t S, int32_t P, int
 }
 
 // Apply one classified message to the book (Sec. 4.2 dispatch; n_bid / n_ask
-// are the warp-uniform side counts).
+// are the warp-uniform side counts).  Every branch is warp-uniform.
 template <int K, class Book>
 __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, int cap, int rule,
                                               int32_t op, int32_t P, int32_t Q, int32_t oid,
-                                              int32_t tid, int64_t tm, TradeSink& ts, Counters& ctr)
+                                              int32_t tid, int32_t tlo, int32_t thi, TradeSink& ts,
+                                              Tally& ctr)
 {
-    switch (op) {
-    case OP_LIMIT_BID: {  // buy limit: match the asks, then rest the remainder as a bid
+    if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
         int32_t rest = Q;
         if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), P))
-            rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tm, ts, ctr);
-        if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tm, ctr);
-        break;
-    }
-    case OP_LIMIT_ASK: {
+            rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr);
+        if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+    } else if (op == OP_LIMIT_ASK) {
         int32_t rest = Q;
         if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), P))
-            rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tm, ts, ctr);
-        if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tm, ctr);
-        break;
-    }
-    case OP_MARKET_BID: {  // market buy: price max_int, remainder dropped
-        int32_t rest = Q;
-        if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tm, ts, ctr);
-        ctr.add(CTR_MARKET_DISCARDED_QTY, rest);
-        break;
-    }
-    case OP_MARKET_ASK: {  // market sell: price 0
-        int32_t rest = Q;
-        if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tm, ts, ctr);
-        ctr.add(CTR_MARKET_DISCARDED_QTY, rest);
-        break;
-    }
-    case OP_CANCEL_BID:  // cancel and delete are treated identically
+            rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr);
+        if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+    } else if (op == OP_CANCEL_BID) {  // cancel and delete are treated identically
         cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
-        break;
-    case OP_CANCEL_ASK:
+    } else if (op == OP_CANCEL_ASK) {
         cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
-        break;
-    default:
-        break;
+    } else if (op == OP_MARKET_BID) {  // market buy: price max_int, remainder dropped
+        int32_t rest = Q;
+        if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr);
+        ctr.discarded_qty += rest;
+    } else if (op == OP_MARKET_ASK) {  // market sell: price 0
+        int32_t rest = Q;
+        if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr);
+        ctr.discarded_qty += rest;
     }
     if constexpr (!Book::kInRegisters) __syncwarp();
 }

@@ -160,6 +160,8 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
         }
         int n_bid = a.counts[2 * b], n_ask = a.counts[2 * b + 1];
         Counters ctr{0, l};
+        Tally tally;
+        const int64_t tcount0 = ts.count;
         Book bk;
         if constexpr (!Book::kInRegisters) bk.base = image;
         // book-independent counters, accumulated by the pre-pass per lane
@@ -204,9 +206,8 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                     na = mb[2 * i + 2];
                     nb = mb[2 * i + 3];
                 }
-                const int64_t tm = (int64_t)(((uint64_t)(uint32_t)hb.w << 32) | (uint32_t)hb.z);
                 apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
-                                 tm, ts, ctr);
+                                 hb.z, hb.w, ts, tally);
             }
             __syncwarp();
             if (c + 2 < nchunks && l == 0) {
@@ -227,6 +228,18 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
 #pragma unroll 4
         for (int i = l; i < Geo<K>::BOOK_BYTES / 16; i += 32) dst[i] = src[i];
         ctr.add(CTR_MSGS, nmsg);
+        ctr.add(CTR_TRADES, ts.count - tcount0);
+        ctr.add(CTR_TRADES_DROPPED, max(ts.count - a.trade_cap, (int64_t)0) -
+                                        max(tcount0 - a.trade_cap, (int64_t)0));
+        ctr.add(CTR_TRADED_QTY, tally.traded_qty);
+        ctr.add(CTR_RESTED, tally.rested);
+        ctr.add(CTR_REJECTED, tally.rejected);
+        ctr.add(CTR_REJECTED_QTY, tally.rejected_qty);
+        ctr.add(CTR_EVICTED, tally.evicted);
+        ctr.add(CTR_EVICTED_QTY, tally.evicted_qty);
+        ctr.add(CTR_CANCEL_HIT, tally.cancel_hit);
+        ctr.add(CTR_CANCELLED_QTY, tally.cancelled_qty);
+        ctr.add(CTR_MARKET_DISCARDED_QTY, tally.discarded_qty);
         ctr.add(CTR_NOOP, __reduce_add_sync(kFull, (unsigned)c_kind[0]));
         ctr.add(CTR_INVALID, __reduce_add_sync(kFull, (unsigned)c_kind[1]));
         ctr.add(CTR_LIMIT, __reduce_add_sync(kFull, (unsigned)c_kind[2]));
