@@ -250,16 +250,16 @@ __device__ __forceinline__ void drop_front(T (&v)[K], int m)
     T r[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) r[j] = v[j];
-    // rotate lane-locally by b (warp-uniform): r[j] = v[(j + b) % K]
+    // rotate lane-locally by b (warp-uniform): r[j] = v[(j + b) % K], by
+    // selects on the bits of b
 #pragma unroll
     for (int bit = 1; bit < K; bit <<= 1) {
-        if (b & bit) {
-            T t[K];
+        const bool on = (b & bit) != 0;
+        T t[K];
 #pragma unroll
-            for (int j = 0; j < K; ++j) t[j] = r[(j + bit) % K];
+        for (int j = 0; j < K; ++j) t[j] = on ? r[(j + bit) % K] : r[j];
 #pragma unroll
-            for (int j = 0; j < K; ++j) r[j] = t[j];
-        }
+        for (int j = 0; j < K; ++j) r[j] = t[j];
     }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
@@ -449,18 +449,18 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
 #pragma unroll
     for (int j = 0; j < K; ++j) cnt += (l * K + j < n && at_least<X>(v.px[j], P)) ? 1u : 0u;
     const int p = (int)__reduce_add_sync(kFull, cnt);
-    int n_after = n + 1;
-    if (n >= cap) {
-        if (rule != 0 || p >= cap) {
-            ctr.rejected += 1;
-            ctr.rejected_qty += Q;
-            return;
-        }
-        // the worst order (slot cap-1) has a strictly worse price: evict it
-        ctr.evicted += 1;
-        ctr.evicted_qty += slot_value<K>(v.q, cap - 1);
-        n_after = cap;
+    const bool full = n >= cap;
+    if (full && (rule != 0 || p >= cap)) {
+        ctr.rejected += 1;
+        ctr.rejected_qty += Q;
+        return;
     }
+    // full side: the worst order (slot cap-1) has a strictly worse price and
+    // is evicted
+    const int32_t q_worst = slot_value<K>(v.q, cap - 1);
+    ctr.evicted += full ? 1 : 0;
+    ctr.evicted_qty += full ? q_worst : 0;
+    const int n_after = full ? cap : n + 1;
     shift_in<K>(v.px, p, n_after, P);
     shift_in<K>(v.q, p, n_after, Q);
     shift_in<K>(v.oid, p, n_after, oid);
@@ -542,18 +542,29 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
         acc = sat_add(acc, cq[j]);
         loc[j] = acc;
     }
-    // warp inclusive scan of the lane totals (saturating at INT32_MAX: exact
-    // wherever the running total is below Q <= INT32_MAX, which is all that
-    // the fills depend on)
-    uint32_t incl = acc;
+    // When the fills end inside lane 0's slots (lane 0 alone covers Q, or the
+    // crossing prefix does not reach lane 1) no warp-wide scan is needed.
+    const unsigned first_crosses = __ballot_sync(kFull, cq[0] != 0u);
+    const uint32_t acc0 = __shfl_sync(kFull, acc, 0);
+    const bool local = acc0 >= (uint32_t)Q || !(first_crosses & 2u);
+    uint32_t excl, total;
+    if (local) {
+        excl = l == 0 ? 0u : (uint32_t)Q;  // lanes other than 0 get no room
+        total = acc0;
+    } else {
+        // warp inclusive scan of the lane totals (saturating at INT32_MAX:
+        // exact wherever the running total is below Q <= INT32_MAX, which is
+        // all that the fills depend on)
+        uint32_t incl = acc;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, d);
-        if (l >= d) incl = sat_add(incl, t);
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(kFull, incl, d);
+            if (l >= d) incl = sat_add(incl, t);
+        }
+        excl = __shfl_up_sync(kFull, incl, 1);
+        if (l == 0) excl = 0;
+        total = __shfl_sync(kFull, incl, 31);
     }
-    uint32_t excl = __shfl_up_sync(kFull, incl, 1);
-    if (l == 0) excl = 0;
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
 
     int32_t fill[K];
     unsigned nfull = 0, nfill = 0;
@@ -565,9 +576,16 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
         nfull += (cq[j] != 0u && (uint32_t)fill[j] == cq[j]) ? 1u : 0u;
         nfill += fill[j] > 0 ? 1u : 0u;
     }
-    const int m = (int)__reduce_add_sync(kFull, nfull);   // fully filled: leave the book
-    const int nf = (int)__reduce_add_sync(kFull, nfill);  // trades of this message
-    const int32_t F = (int32_t)min(total, (uint32_t)Q);    // quantity traded
+    int m, nf;  // fully filled orders (they leave the book), trades of this message
+    if (local) {
+        const unsigned packed = __shfl_sync(kFull, nfull | (nfill << 16), 0);
+        m = (int)(packed & 0xffffu);
+        nf = (int)(packed >> 16);
+    } else {
+        m = (int)__reduce_add_sync(kFull, nfull);
+        nf = (int)__reduce_add_sync(kFull, nfill);
+    }
+    const int32_t F = (int32_t)min(total, (uint32_t)Q);  // quantity traded
 
     // trades: the filled slots are the prefix [0, nf), trade k -> slot k
 #pragma unroll
@@ -643,27 +661,30 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
                                               int32_t tid, int32_t tlo, int32_t thi, TradeSink& ts,
                                               Tally& ctr)
 {
-    if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
+    if (op <= OP_LIMIT_ASK) {
+        if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
+            int32_t rest = Q;
+            if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), P))
+                rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr);
+            if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+        } else if (op == OP_LIMIT_ASK) {
+            int32_t rest = Q;
+            if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), P))
+                rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr);
+            if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+        }
+    } else if (op <= OP_CANCEL_ASK) {  // cancel and delete are treated identically
+        if (op == OP_CANCEL_BID)
+            cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
+        else
+            cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
+    } else {  // market: price max_int (buy) / 0 (sell), remainder dropped
         int32_t rest = Q;
-        if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), P))
-            rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr);
-        if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
-    } else if (op == OP_LIMIT_ASK) {
-        int32_t rest = Q;
-        if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), P))
-            rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr);
-        if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
-    } else if (op == OP_CANCEL_BID) {  // cancel and delete are treated identically
-        cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
-    } else if (op == OP_CANCEL_ASK) {
-        cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
-    } else if (op == OP_MARKET_BID) {  // market buy: price max_int, remainder dropped
-        int32_t rest = Q;
-        if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr);
-        ctr.discarded_qty += rest;
-    } else if (op == OP_MARKET_ASK) {  // market sell: price 0
-        int32_t rest = Q;
-        if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr);
+        if (op == OP_MARKET_BID) {
+            if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr);
+        } else {
+            if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr);
+        }
         ctr.discarded_qty += rest;
     }
     if constexpr (!Book::kInRegisters) __syncwarp();
