@@ -268,6 +268,18 @@ __device__ __forceinline__ void drop_front(T (&v)[K], int m)
     }
 }
 
+// drop_front for a compile-time 0 < M < K: new slot s takes old slot s + M;
+// only the first M values of the next lane cross lanes.
+template <int K, int M, typename T>
+__device__ __forceinline__ void drop_front_small(T (&v)[K])
+{
+    T nxt[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) nxt[j] = __shfl_down_sync(kFull, v[j], 1);
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = (j + M < K) ? v[j + M] : nxt[j + M - K];
+}
+
 // Does this lane own a slot in [lo, hi)?
 template <int K>
 __device__ __forceinline__ bool lane_touches(int lo, int hi)
@@ -508,6 +520,33 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
     n -= 1;
 }
 
+// Remove the first m (0 < m < K) slots of every field: a uniform switch over
+// the few possible values keeps every register index static.
+template <int K, int M>
+__device__ __forceinline__ void drop_front_fields(SideVec<K>& v)
+{
+    if constexpr (M > 0 && M < K) {
+        drop_front_small<K, M>(v.px);
+        drop_front_small<K, M>(v.q);
+        drop_front_small<K, M>(v.oid);
+        drop_front_small<K, M>(v.tid);
+        drop_front_small<K, M>(v.tlo);
+        drop_front_small<K, M>(v.thi);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void drop_front_small_all(SideVec<K>& v, int m)
+{
+    if (m == 1) drop_front_fields<K, 1>(v);
+    else if (m == 2) drop_front_fields<K, 2>(v);
+    else if (m == 3) drop_front_fields<K, 3>(v);
+    else if (m == 4) drop_front_fields<K, 4>(v);
+    else if (m == 5) drop_front_fields<K, 5>(v);
+    else if (m == 6) drop_front_fields<K, 6>(v);
+    else drop_front_fields<K, 7>(v);
+}
+
 // Where trades of the current book go and how many are already there.
 struct TradeSink {
     Trade* log;      // this book's segment of the trade log
@@ -588,11 +627,13 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
     const int32_t F = (int32_t)min(total, (uint32_t)Q);  // quantity traded
 
     // trades: the filled slots are the prefix [0, nf), trade k -> slot k
+    // slots [0, n_store) still fit in the log
+    const int n_store = (int)max(min((int64_t)nf, (int64_t)ts.cap - ts.count), (int64_t)0);
+    Trade* const log_at = ts.log + ts.count;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const int64_t idx = ts.count + l * K + j;
-        if (fill[j] > 0 && idx < ts.cap) {
-            int4* dst = reinterpret_cast<int4*>(ts.log + idx);
+        if (l * K + j < n_store) {
+            int4* dst = reinterpret_cast<int4*>(log_at + l * K + j);
             dst[0] = make_int4(v.px[j], fill[j], oid_a, v.oid[j]);
             dst[1] = make_int4(tid_a, v.tid[j], tlo, thi);
         }
@@ -605,12 +646,16 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
 #pragma unroll
     for (int j = 0; j < K; ++j) v.q[j] -= fill[j];
     if (m > 0) {
-        drop_front<K>(v.px, m);
-        drop_front<K>(v.q, m);
-        drop_front<K>(v.oid, m);
-        drop_front<K>(v.tid, m);
-        drop_front<K>(v.tlo, m);
-        drop_front<K>(v.thi, m);
+        if (m < K && K <= 8) {
+            drop_front_small_all<K>(v, m);
+        } else {
+            drop_front<K>(v.px, m);
+            drop_front<K>(v.q, m);
+            drop_front<K>(v.oid, m);
+            drop_front<K>(v.tid, m);
+            drop_front<K>(v.tlo, m);
+            drop_front<K>(v.thi, m);
+        }
         bk.template release<Y>(v, lane_touches<K>(0, n - m));
         n -= m;
     } else if (nf > 0) {
