@@ -14,7 +14,7 @@ Two independent CPU implementations live here:
   formulation (Sec. 4 eqs. 1-2, Sec. 4.1), used only to cross-check the oracle
   by brute force on tiny books.
 
-``lob_env_oracle.cpp`` (class :class:`EnvOracle`) adds the execution-environment
+``lob_oracle.cpp`` also holds (class :class:`EnvOracle`) the execution-environment
 step of Sec. 5 (replay, then the synthetic agent's orders, top levels, agent
 fills and the VWAP reward of eqs. rewardfunc / vwap).
 
@@ -35,7 +35,6 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 ORACLE_SO = os.path.join(HERE, "liblob_oracle.so")
 LITERAL_SO = os.path.join(HERE, "liblob_literal.so")
-ENV_SO = os.path.join(HERE, "liblob_env_oracle.so")
 
 MSG_DTYPE = np.dtype([("type", "<i4"), ("side", "<i4"), ("price", "<i4"), ("qty", "<i4"),
                       ("oid", "<i4"), ("tid", "<i4"), ("time_ns", "<i8")])
@@ -60,7 +59,6 @@ def build(force: bool = False) -> None:
     jobs = [
         (ORACLE_SO, ["lob_oracle.cpp"], ["g++", "-O2", "-std=c++17"]),
         (LITERAL_SO, ["lob_literal.c"], ["gcc", "-O2", "-std=c11"]),
-        (ENV_SO, ["lob_env_oracle.cpp", "lob_oracle.cpp"], ["g++", "-O2", "-std=c++17"]),
     ]
     for so, srcs, cc in jobs:
         paths = [os.path.join(HERE, s) for s in srcs]
@@ -113,9 +111,13 @@ class Oracle:
     """n_books independent books; the same call sequence as the engine's C ABI."""
 
     def __init__(self, n_books: int, capacity: int, trade_capacity: int,
-                 overflow_rule: int = 0, append_trades: bool = False):
+                 overflow_rule: int = 0, append_trades: bool = False, _borrow=None):
         self.lib = _oracle_lib()
         self.n_books, self.capacity, self.trade_capacity = n_books, capacity, trade_capacity
+        if _borrow is not None:  # books owned by an EnvOracle
+            self.h, self._owned = _borrow, False
+            return
+        self._owned = True
         self.h = self.lib.oracle_create(n_books, capacity, trade_capacity, overflow_rule,
                                         1 if append_trades else 0)
         if not self.h:
@@ -123,7 +125,7 @@ class Oracle:
 
     def __del__(self):
         h = getattr(self, "h", None)
-        if h:
+        if h and getattr(self, "_owned", False):
             self.lib.oracle_destroy(h)
             self.h = None
 
@@ -209,3 +211,54 @@ def literal_run(msgs: np.ndarray, offsets: np.ndarray, capacity: int, trade_capa
 def messages(rows) -> np.ndarray:
     """Build a message array from (type, side, price, qty, oid, tid, time_ns) tuples."""
     return np.array([tuple(r) for r in rows], dtype=MSG_DTYPE)
+
+
+class EnvOracle:
+    """Execution-environment steps (Sec. 5) over n_envs books, see lob_oracle.cpp."""
+
+    STATE_FIELDS = ["submitted", "executed", "id_counter", "last_ask", "last_time"]
+
+    def __init__(self, n_envs, capacity, trade_capacity, n_steps=400, parent_qty=2000,
+                 agent_tid=1_000_000, depth=10, p_init_fallback=10_000, lam=0.0):
+        lib = _oracle_lib()
+        vp, i32 = ctypes.c_void_p, ctypes.c_int32
+        lib.oracle_env_create.restype = vp
+        lib.oracle_env_create.argtypes = [i32] * 8 + [ctypes.c_double]
+        lib.oracle_env_destroy.argtypes = [vp]
+        lib.oracle_env_books.restype = vp
+        lib.oracle_env_books.argtypes = [vp]
+        lib.oracle_env_step.argtypes = [vp, vp, vp, vp, i32] + [vp] * 6 + [i32]
+        lib.oracle_env_state.argtypes = [vp, vp, vp]
+        self.lib = lib
+        self.n, self.depth = n_envs, depth
+        self.h = lib.oracle_env_create(n_envs, capacity, trade_capacity, n_steps, parent_qty,
+                                       agent_tid, depth, p_init_fallback, float(lam))
+        if not self.h:
+            raise ValueError("invalid environment configuration")
+        self.books = Oracle(n_envs, capacity, trade_capacity,
+                            _borrow=lib.oracle_env_books(self.h))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.oracle_env_destroy(h)
+            self.h = None
+
+    def step(self, replay, offsets, draws, step, threads=None):
+        replay = np.ascontiguousarray(replay, dtype=MSG_DTYPE)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        draws = np.ascontiguousarray(draws, dtype=np.uint32)
+        n, d = self.n, self.depth
+        reward = np.empty(n, np.float32)
+        lv = [np.empty((n, d), np.int32) for _ in range(4)]
+        fills = np.empty((n, 2), np.int64)
+        self.lib.oracle_env_step(self.h, _p(replay) if len(replay) else None, _p(offsets),
+                                 _p(draws), step, _p(reward), *[_p(x) for x in lv], _p(fills),
+                                 threads or default_threads())
+        return reward, tuple(lv), fills
+
+    def state(self):
+        out = np.empty((self.n, 5), np.int64)
+        p0 = np.empty(self.n, np.float64)
+        self.lib.oracle_env_state(self.h, _p(out), _p(p0))
+        return out, p0

@@ -162,8 +162,16 @@ struct Side {
     }
 };
 
+// Per-step trade sums of the execution environment (Sec. 5.2.4): all trades
+// of the step, and those of the agent (trader id `agent_tid`).
+struct StepSums {
+    int64_t sq = 0, spq = 0, aq = 0, apq = 0;
+    int32_t agent_tid = 0;
+};
+
 struct Book {
     Side bids{true}, asks{false};
+    StepSums* sums = nullptr;  // set while an environment step observes trades
     std::vector<Trade> log;   // stored trades of the current call (<= trade capacity)
     int64_t log_count = 0;    // trades executed during the current call
     int64_t counters[N_COUNTERS] = {};
@@ -189,6 +197,15 @@ static void log_trade(Engine& E, Book& bk, const Trade& t)
     bk.log_count += 1;
     bk.counters[C_TRADES] += 1;
     bk.counters[C_TRADED_QTY] += t.qty;
+    if (bk.sums) {
+        StepSums& s = *bk.sums;
+        s.sq += t.qty;
+        s.spq += (int64_t)t.qty * t.price;
+        if (t.tid_aggr == s.agent_tid || t.tid_stand == s.agent_tid) {
+            s.aq += t.qty;
+            s.apq += (int64_t)t.qty * t.price;
+        }
+    }
 }
 
 // Matching (Sec. 4.1 item 3 and the while loop that follows it).
@@ -454,12 +471,21 @@ int oracle_set_book(void* h, const int32_t* px, const int32_t* qty, const int32_
 
 // Top `depth` price levels per side: aggregated quantity per distinct price,
 // best first; empty levels are (-1, 0).  Quantities saturate at max_int.
+static void book_levels(Book& bk, int32_t b, int32_t depth, int32_t* bid_px, int32_t* bid_qty,
+                        int32_t* ask_px, int32_t* ask_qty);
+
 void oracle_get_levels(void* h, int32_t depth, int32_t* bid_px, int32_t* bid_qty, int32_t* ask_px,
                        int32_t* ask_qty)
 {
     Engine& E = *(Engine*)h;
-    for (int32_t b = 0; b < E.n_books; ++b) {
-        Book& bk = E.books[(size_t)b];
+    for (int32_t b = 0; b < E.n_books; ++b)
+        book_levels(E.books[(size_t)b], b, depth, bid_px, bid_qty, ask_px, ask_qty);
+}
+
+static void book_levels(Book& bk, int32_t b, int32_t depth, int32_t* bid_px, int32_t* bid_qty,
+                        int32_t* ask_px, int32_t* ask_qty)
+{
+    {
         for (int s = 0; s < 2; ++s) {
             Side& sd = s == 0 ? bk.bids : bk.asks;
             int32_t* opx = (s == 0 ? bid_px : ask_px) + (int64_t)b * depth;
@@ -506,6 +532,203 @@ void oracle_get_resting_qty(void* h, int64_t* out)
             sd.for_each([&](const Order& o) { sum += o.qty; });
         }
         out[b] = sum;
+    }
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// Execution environment (Sec. 5): each book is one environment whose step
+// replays a window of data messages, then submits the agent's orders, then
+// reports the top levels, the agent's fills and the reward
+//   R = sum_j Q_j (P_j - P_VWAP) + lambda * sum_j Q_j (P_VWAP - P_init),
+//   P_VWAP = sum_i Q_i P_i / sum_i Q_i                  (eqs. rewardfunc, vwap)
+// with i over every trade of the step and j over the agent's trades.
+// The agent (not specified by the paper; a seeded stand-in for the learned
+// policy) sells a parent order of `parent_qty` over `n_steps` steps: at step
+// t < n_steps-1 it splits ceil((parent - submitted) / (n_steps - t)) into
+// n in {1..4} child sell orders (equal parts, remainder to the first, empty
+// parts dropped), each a limit at last_ask + {-2..+2} ticks (at least 1) or a
+// market order, as drawn; at the last step it cancels its resting orders and
+// sends a market sell for parent - executed (Sec. 5.2.5).
+// Agent orders carry oid 2^30 + counter (the ID counter of Sec. 5.1.2) and the
+// time of the step's last data message (Sec. 5.1.3 step 3).
+namespace oracle {
+
+struct EnvCfg {
+    int32_t n_steps, parent_qty, agent_tid, depth, p_init_fallback;
+    double lambda;
+};
+
+struct EnvState {
+    int64_t submitted = 0, executed = 0;
+    int32_t id_counter = 0, last_ask = 0;
+    int64_t last_time = 0;
+    double p_init = 0.0;
+};
+
+struct EnvEngine {
+    Engine E;
+    EnvCfg cfg;
+    std::vector<EnvState> st;
+};
+
+static int32_t best_price(Side& sd)
+{
+    return sd.best().price;
+}
+
+static void env_step_one(EnvEngine& V, int32_t b, const Msg* msgs, int64_t n_msgs, uint32_t draw,
+                         int32_t t, float* reward, int32_t* bid_px, int32_t* bid_qty,
+                         int32_t* ask_px, int32_t* ask_qty, int64_t* fills)
+{
+    Engine& E = V.E;
+    const EnvCfg& cfg = V.cfg;
+    EnvState& es = V.st[(size_t)b];
+    Book& bk = E.books[(size_t)b];
+    bk.log.clear();
+    bk.log_count = 0;
+    StepSums sums;
+    sums.agent_tid = cfg.agent_tid;
+    bk.sums = &sums;
+
+    // 1. replay the step's data messages
+    for (int64_t k = 0; k < n_msgs; ++k) process(E, bk, msgs[k]);
+    if (n_msgs > 0) es.last_time = msgs[n_msgs - 1].time_ns;
+
+    // 2. initial mid-price of the episode (after the first data window)
+    if (t == 0) {
+        const bool hb = !bk.bids.empty(), ha = !bk.asks.empty();
+        if (hb && ha)
+            es.p_init = ((double)best_price(bk.bids) + (double)best_price(bk.asks)) / 2.0;
+        else if (hb)
+            es.p_init = (double)best_price(bk.bids);
+        else if (ha)
+            es.p_init = (double)best_price(bk.asks);
+        else
+            es.p_init = (double)cfg.p_init_fallback;
+    }
+
+    // 3. the agent's orders
+    auto send = [&](int32_t type, int32_t price, int32_t qty) {
+        Msg m;
+        m.type = type;
+        m.side = -1;
+        m.price = price;
+        m.qty = qty;
+        m.oid = (int32_t)((1u << 30) + (uint32_t)es.id_counter);
+        m.tid = cfg.agent_tid;
+        m.time_ns = es.last_time;
+        es.id_counter += 1;
+        es.submitted += qty;
+        process(E, bk, m);
+    };
+    if (t < cfg.n_steps - 1) {
+        if (!bk.asks.empty()) es.last_ask = best_price(bk.asks);
+        const int64_t remaining = cfg.parent_qty - es.submitted;
+        const int64_t steps_left = cfg.n_steps - t;
+        const int64_t target = remaining > 0 ? (remaining + steps_left - 1) / steps_left : 0;
+        const int32_t n = (int32_t)(draw & 3u) + 1;
+        const int64_t base = target / n, extra = target % n;
+        for (int32_t k = 0; k < n; ++k) {
+            const int32_t q = (int32_t)(base + (k == 0 ? extra : 0));
+            if (q <= 0) continue;
+            const int32_t a = (int32_t)((draw >> (2 + 3 * k)) & 7u);
+            if (a == 5)
+                send(4, 0, q);
+            else
+                send(1, std::max(1, es.last_ask + a - 2), q);
+        }
+    } else {
+        // cancel the agent's resting orders (priority order), then sell the rest
+        std::vector<Order> mine;
+        bk.asks.for_each([&](const Order& o) {
+            if (o.tid == cfg.agent_tid) mine.push_back(o);
+        });
+        for (const Order& o : mine) {
+            Msg m;
+            m.type = 2;
+            m.side = -1;
+            m.price = o.price;
+            m.qty = o.qty;
+            m.oid = o.oid;
+            m.tid = cfg.agent_tid;
+            m.time_ns = es.last_time;
+            process(E, bk, m);
+        }
+        const int64_t left = cfg.parent_qty - (es.executed + sums.aq);
+        if (left > 0) send(4, 0, (int32_t)left);
+    }
+    bk.sums = nullptr;
+    es.executed += sums.aq;
+
+    // 4. reward (eqs. rewardfunc, vwap), IEEE double, fixed operation order
+    double r = 0.0;
+    if (sums.sq > 0 && sums.aq > 0) {
+        const double vwap = (double)sums.spq / (double)sums.sq;
+        const double adv = (double)sums.apq - (double)sums.aq * vwap;
+        const double drift = cfg.lambda * ((double)sums.aq * (vwap - es.p_init));
+        r = adv + drift;
+    }
+    reward[b] = (float)r;
+    fills[2 * (int64_t)b] = sums.aq;
+    fills[2 * (int64_t)b + 1] = sums.apq;
+    book_levels(bk, b, cfg.depth, bid_px, bid_qty, ask_px, ask_qty);
+}
+
+}  // namespace oracle
+
+extern "C" {
+
+void* oracle_env_create(int32_t n_envs, int32_t capacity, int32_t trade_capacity, int32_t n_steps,
+                        int32_t parent_qty, int32_t agent_tid, int32_t depth,
+                        int32_t p_init_fallback, double lambda)
+{
+    if (n_envs < 1 || capacity < 1 || trade_capacity < 0 || n_steps < 1 || parent_qty < 0 ||
+        depth < 1)
+        return nullptr;
+    EnvEngine* V = new EnvEngine();
+    V->E.n_books = n_envs;
+    V->E.capacity = capacity;
+    V->E.trade_capacity = trade_capacity;
+    V->E.overflow_rule = 0;
+    V->E.append_trades = false;
+    V->E.books.resize((size_t)n_envs);
+    V->cfg = EnvCfg{n_steps, parent_qty, agent_tid, depth, p_init_fallback, lambda};
+    V->st.assign((size_t)n_envs, EnvState());
+    for (auto& s : V->st) s.last_ask = p_init_fallback;
+    return V;
+}
+
+void oracle_env_destroy(void* h) { delete (EnvEngine*)h; }
+
+// The books of the environments, usable with every oracle_get_* accessor.
+void* oracle_env_books(void* h) { return &((EnvEngine*)h)->E; }
+
+// One step for every environment: env b replays replay[offsets[b] .. offsets[b+1]).
+void oracle_env_step(void* h, const Msg* replay, const int64_t* offsets, const uint32_t* draws,
+                     int32_t step, float* reward, int32_t* bid_px, int32_t* bid_qty,
+                     int32_t* ask_px, int32_t* ask_qty, int64_t* fills, int32_t n_threads)
+{
+    EnvEngine& V = *(EnvEngine*)h;
+    parallel_for(V.E.n_books, n_threads, [&](int32_t b) {
+        env_step_one(V, b, replay + offsets[b], offsets[b + 1] - offsets[b], draws[b], step, reward,
+                     bid_px, bid_qty, ask_px, ask_qty, fills);
+    });
+}
+
+// per env: submitted, executed, id_counter, last_ask, last_time; and p_init
+void oracle_env_state(void* h, int64_t* out, double* p_init)
+{
+    EnvEngine& V = *(EnvEngine*)h;
+    for (size_t b = 0; b < V.st.size(); ++b) {
+        const EnvState& s = V.st[b];
+        out[5 * b + 0] = s.submitted;
+        out[5 * b + 1] = s.executed;
+        out[5 * b + 2] = s.id_counter;
+        out[5 * b + 3] = s.last_ask;
+        out[5 * b + 4] = s.last_time;
+        p_init[b] = s.p_init;
     }
 }
 
