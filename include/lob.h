@@ -210,6 +210,71 @@ int lob_set_book(lob_ctx* ctx, const int32_t* d_price, const int32_t* d_qty,
  * the status word (int32, LOB_STATUS_* bits).  Either pointer may be NULL. */
 int lob_get_stats(lob_ctx* ctx, int64_t* d_counters, int32_t* d_status, void* stream);
 
+/* ------------------------------------------------- execution environment */
+
+/* One environment per book of a context (Sec. 5, gymnax base and execution
+ * environments): each step replays a window of data messages, then submits the
+ * agent's orders, then reports the top levels, the agent's fills and the
+ * reward R = sum_j Q_j (P_j - P_VWAP) + lambda * sum_j Q_j (P_VWAP - P_init)
+ * with P_VWAP = sum_i Q_i P_i / sum_i Q_i (Sec. 5.2.4, eqs. rewardfunc and
+ * vwap; i over all trades of the step, j over the agent's trades; R = 0 when
+ * the step has no trade or no agent trade; P_init = mid after the first
+ * step's data, or the one-sided best price, or p_init_fallback).  The reward
+ * is evaluated in IEEE double in that operation order and rounded to float.
+ *
+ * The agent (a seeded stand-in for the learned policy) sells parent_qty over
+ * n_steps steps: at step t < n_steps-1 it splits
+ * ceil((parent_qty - submitted) / (n_steps - t)) into the number of child
+ * orders its draw gives (equal parts, remainder to the first, empty parts
+ * dropped), each a limit sell at last_ask + {-2..+2} ticks (at least 1; last_ask
+ * = best ask when the ask side is non-empty) or a market sell; at the last
+ * step it cancels its resting orders in priority order and sells
+ * parent_qty - executed at market (Sec. 5.2.5).  Agent orders carry
+ * oid 2^30 + counter, tid agent_tid and the time of the step's last data
+ * message (Sec. 5.1.3).  Draws are uint32: bits 0-1 = child orders - 1,
+ * bits 2+3k..4+3k = action of child k (0..4 = -2..+2 ticks, 5 = market). */
+typedef struct {
+    int32_t n_steps;          /* episode length                                 */
+    int32_t parent_qty;       /* shares the agent sells over the episode         */
+    int32_t agent_tid;        /* trader id of the agent's orders                 */
+    int32_t depth;            /* levels per side in the step output, 1..64       */
+    int32_t p_init_fallback;  /* initial mid / last_ask when a side is empty     */
+    int32_t msgs_per_step;    /* data messages per step, 1..1024                 */
+    double lambda;            /* drift weight of eq. rewardfunc                  */
+} lob_env_config_t;
+
+typedef struct lob_env lob_env;
+
+/* Create the environments of every book of `book` (which must outlive them)
+ * and set their agent state to the start of an episode.  Books are not
+ * touched (lob_reset empties them). */
+int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, void* stream);
+int lob_env_destroy(lob_env* env);
+
+/* Agent state back to the start of an episode (submitted = executed = 0,
+ * counter 0, last_ask = p_init_fallback). */
+int lob_env_reset(lob_env* env, void* stream);
+
+/* Run steps step0 .. step0+n_run-1 of every environment in ONE launch (the
+ * books stay in on-chip memory across the steps).  n_run = 1 is one step.
+ *   d_replay : data messages, 16-byte aligned; env b's step t window is
+ *              d_replay[b*stride_env + t*msgs_per_step ..][0 .. msgs_per_step)
+ *   d_draws  : uint32[n_run][n_books] agent draws of those steps
+ *   outputs, each [n_run][n_books][...]: d_reward float; d_bid_px, d_bid_qty,
+ *   d_ask_px, d_ask_qty int32 [depth]; d_fills int64 [2] = agent quantity and
+ *   agent sum of Q*P of the step.
+ * After the call the book's trade log holds the trades of the last step run.
+ * Errors: LOB_E_INVAL when a step is outside [0, n_steps) or an argument is
+ * bad. */
+int lob_env_run(lob_env* env, const lob_msg_t* d_replay, int64_t stride_env, int32_t step0,
+                int32_t n_run, const uint32_t* d_draws, float* d_reward, int32_t* d_bid_px,
+                int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty, int64_t* d_fills,
+                void* stream);
+
+/* Agent state: int64[n_books][5] = submitted, executed, id counter, last_ask,
+ * last data time; double[n_books] = P_init.  Either pointer may be NULL. */
+int lob_env_get_state(lob_env* env, int64_t* d_state, double* d_p_init, void* stream);
+
 /* ------------------------------------------------------ allocation-free call */
 
 /* No counterpart in the paper: an engineering addition for callers that must

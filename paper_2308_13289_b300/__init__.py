@@ -16,7 +16,7 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import LobConfig, LobError, check
+from ._abi import LobConfig, LobEnvConfig, LobError, check
 
 OVERFLOW_EVICT, OVERFLOW_REJECT = 0, 1
 FLAG_APPEND_TRADES = 1
@@ -141,6 +141,36 @@ def lob_process_streams_static(msgs, offsets, n_books, capacity, trade_capacity,
         "lob_process_streams_static")
 
 
+def lob_env_create(h, n_steps, parent_qty, agent_tid, depth, p_init_fallback, msgs_per_step,
+                   lam=0.0, stream=None):
+    e = ctypes.c_void_p()
+    cfg = LobEnvConfig(n_steps, parent_qty, agent_tid, depth, p_init_fallback, msgs_per_step,
+                       float(lam))
+    check(lib().lob_env_create(ctypes.byref(e), h, ctypes.byref(cfg), _stream(stream)),
+          "lob_env_create")
+    return e
+
+
+def lob_env_destroy(e):
+    check(lib().lob_env_destroy(e), "lob_env_destroy")
+
+
+def lob_env_reset(e, stream=None):
+    check(lib().lob_env_reset(e, _stream(stream)), "lob_env_reset")
+
+
+def lob_env_run(e, replay, stride_env, step0, n_run, draws, reward, bid_px, bid_qty, ask_px,
+                ask_qty, fills, stream=None):
+    check(lib().lob_env_run(e, _ptr(replay), stride_env, step0, n_run, _ptr(draws), _ptr(reward),
+                            _ptr(bid_px), _ptr(bid_qty), _ptr(ask_px), _ptr(ask_qty), _ptr(fills),
+                            _stream(stream)), "lob_env_run")
+
+
+def lob_env_get_state(e, state, p_init, stream=None):
+    check(lib().lob_env_get_state(e, _ptr(state), _ptr(p_init), _stream(stream)),
+          "lob_env_get_state")
+
+
 # ------------------------------------------------------------------ convenience object
 
 class Engine:
@@ -218,6 +248,57 @@ class Engine:
         return ctr, st
 
 
+class Env:
+    """Execution environments over the books of an Engine (see lob_env_* in lob.h)."""
+
+    def __init__(self, engine: "Engine", n_steps=400, parent_qty=2000, agent_tid=1_000_000,
+                 depth=10, p_init_fallback=10_000, msgs_per_step=100, lam=0.0, stream=None):
+        self.engine, self.n, self.depth, self.stream = engine, engine.n_books, depth, stream
+        self.n_steps, self.msgs_per_step = n_steps, msgs_per_step
+        self.h = lob_env_create(engine.h, n_steps, parent_qty, agent_tid, depth, p_init_fallback,
+                                msgs_per_step, lam, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lob_env_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        lob_env_reset(self.h, self.stream)
+
+    def outputs(self, n_run):
+        n, d = self.n, self.depth
+        return dict(reward=torch.empty((n_run, n), dtype=torch.float32, device="cuda"),
+                    bid_px=torch.empty((n_run, n, d), dtype=torch.int32, device="cuda"),
+                    bid_qty=torch.empty((n_run, n, d), dtype=torch.int32, device="cuda"),
+                    ask_px=torch.empty((n_run, n, d), dtype=torch.int32, device="cuda"),
+                    ask_qty=torch.empty((n_run, n, d), dtype=torch.int32, device="cuda"),
+                    fills=torch.empty((n_run, n, 2), dtype=torch.int64, device="cuda"))
+
+    def run(self, replay, stride_env, step0, n_run, draws, out=None, row0=0):
+        """Steps step0..step0+n_run-1; draws int32/uint32 [n_run, n]; results go to
+        rows row0.. of `out` (allocated when None)."""
+        if out is None:
+            out = self.outputs(n_run)
+            row0 = 0
+        sl = {k: v[row0:row0 + n_run] for k, v in out.items()}
+        lob_env_run(self.h, replay, stride_env, step0, n_run, draws, sl["reward"], sl["bid_px"],
+                    sl["bid_qty"], sl["ask_px"], sl["ask_qty"], sl["fills"], self.stream)
+        return out
+
+    def state(self):
+        st = torch.empty((self.n, 5), dtype=torch.int64, device="cuda")
+        p0 = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        lob_env_get_state(self.h, st, p0, self.stream)
+        return st, p0
+
+
 __all__ = [n for n in dir() if n.startswith("lob_")] + [
-    "Engine", "LobError", "messages_to_device", "trades_to_numpy", "MSG_DTYPE", "TRADE_DTYPE",
+    "Engine", "Env", "LobError", "messages_to_device", "trades_to_numpy", "MSG_DTYPE", "TRADE_DTYPE",
     "COUNTERS", "N_COUNTERS"]

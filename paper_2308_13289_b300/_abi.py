@@ -17,6 +17,11 @@ class LobConfig(ctypes.Structure):
                 ("overflow_rule", i32), ("flags", i32)]
 
 
+class LobEnvConfig(ctypes.Structure):
+    _fields_ = [("n_steps", i32), ("parent_qty", i32), ("agent_tid", i32), ("depth", i32),
+                ("p_init_fallback", i32), ("msgs_per_step", i32), ("lam", ctypes.c_double)]
+
+
 # name -> (restype, argtypes); every symbol of include/lob.h
 SIGNATURES = {
     "lob_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(LobConfig), vp]),
@@ -33,6 +38,11 @@ SIGNATURES = {
     "lob_set_launch": (ctypes.c_int, [vp, i32, i32, i32]),
     "lob_launch_count": (i64, [vp]),
     "lob_process_streams_static": (ctypes.c_int, [vp, vp, i32, i32, i32, i32] + [vp] * 10 + [vp]),
+    "lob_env_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, ctypes.POINTER(LobEnvConfig), vp]),
+    "lob_env_destroy": (ctypes.c_int, [vp]),
+    "lob_env_reset": (ctypes.c_int, [vp, vp]),
+    "lob_env_run": (ctypes.c_int, [vp, vp, i64, i32, i32] + [vp] * 7 + [vp]),
+    "lob_env_get_state": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_last_error": (ctypes.c_char_p, []),
     "lob_abi_version": (ctypes.c_int, []),
 }

@@ -425,6 +425,24 @@ struct SmemBook {
     __device__ __forceinline__ void to_image(char*) const {}
 };
 
+// Books whose two sides fit in registers (2 sides x 6 words x K per lane) stay
+// there for the whole stream; the largest capacity works in shared memory.
+template <int K>
+struct BookPolicy {
+    using type = RegBook<K>;
+};
+template <>
+struct BookPolicy<16> {
+    using type = SmemBook<16>;
+};
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t x)
+{
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
+    return x;
+}
+
 // Per-lane counter slot: lane i accumulates counter i of the current book.
 struct Counters {
     int64_t v;
@@ -547,6 +565,35 @@ __device__ __forceinline__ void drop_front_small_all(SideVec<K>& v, int m)
     else drop_front_fields<K, 7>(v);
 }
 
+// Fill observers: NoObs (plain processing) and VwapObs (execution
+// environment: per-lane partial sums of Q*P over all fills and of Q, Q*P over
+// the agent's fills -- reduced once per step, Sec. 5.2.4).
+struct NoObs {
+    template <int K>
+    __device__ __forceinline__ void on_fills(const int32_t (&)[K], const int32_t (&)[K],
+                                             const int32_t (&)[K], int32_t)
+    {
+    }
+};
+
+struct VwapObs {
+    int64_t spq = 0, aq = 0, apq = 0;  // this lane's partial sums
+    int32_t agent_tid = 0;
+    template <int K>
+    __device__ __forceinline__ void on_fills(const int32_t (&fill)[K], const int32_t (&px)[K],
+                                             const int32_t (&tid)[K], int32_t tid_a)
+    {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int64_t qp = (int64_t)fill[j] * px[j];
+            const bool agent = tid_a == agent_tid || tid[j] == agent_tid;
+            spq += qp;
+            aq += agent ? fill[j] : 0;
+            apq += agent ? qp : 0;
+        }
+    }
+};
+
 // Where trades of the current book go and how many are already there.
 struct TradeSink {
     Trade* log;      // this book's segment of the trade log
@@ -562,10 +609,10 @@ struct TradeSink {
 // slot s therefore receives min(Q_s, max(0, Q - (quantity of slots before s))),
 // which one saturating warp prefix scan gives for all slots at once.
 // Returns the aggressor's remaining quantity max(0, Q_a).
-template <int K, int Y, class Book>
+template <int K, int Y, class Book, class Obs>
 __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int32_t Q, int32_t oid_a,
                                                int32_t tid_a, int32_t tlo, int32_t thi,
-                                               TradeSink& ts, Tally& ctr)
+                                               TradeSink& ts, Tally& ctr, Obs& obs)
 {
     const int l = lane_id();
     SideVec<K> tmp;
@@ -640,6 +687,7 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
     }
     ts.count += nf;
     ctr.traded_qty += F;
+    obs.template on_fills<K>(fill, v.px, v.tid, tid_a);
 
     // standing quantities after the fills (Q_s' per slot), then drop the m
     // fully filled orders at the front (Q <= 0 cleanup)
@@ -700,22 +748,22 @@ __device__ __forceinline__ int32_t classify(int32_t T, int32_t S, int32_t P, int
 
 // Apply one classified message to the book (Sec. 4.2 dispatch; n_bid / n_ask
 // are the warp-uniform side counts).  Every branch is warp-uniform.
-template <int K, class Book>
+template <int K, class Book, class Obs>
 __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, int cap, int rule,
                                               int32_t op, int32_t P, int32_t Q, int32_t oid,
                                               int32_t tid, int32_t tlo, int32_t thi, TradeSink& ts,
-                                              Tally& ctr)
+                                              Tally& ctr, Obs& obs)
 {
     if (op <= OP_LIMIT_ASK) {
         if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
             int32_t rest = Q;
             if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), P))
-                rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr);
+                rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
             if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
         } else if (op == OP_LIMIT_ASK) {
             int32_t rest = Q;
             if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), P))
-                rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr);
+                rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
             if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
         }
     } else if (op <= OP_CANCEL_ASK) {  // cancel and delete are treated identically
@@ -726,13 +774,58 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
     } else {  // market: price max_int (buy) / 0 (sell), remainder dropped
         int32_t rest = Q;
         if (op == OP_MARKET_BID) {
-            if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr);
+            if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr, obs);
         } else {
-            if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr);
+            if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr, obs);
         }
         ctr.discarded_qty += rest;
     }
     if constexpr (!Book::kInRegisters) __syncwarp();
+}
+
+// Top `depth` price levels of one side whose lane vectors are px/q with n
+// live slots (Sec. 5.1.1 ten-level state): level k = k-th distinct price in
+// priority order with the summed quantity of its orders (saturating at
+// INT32_MAX); missing levels are (-1, 0).  lq/lp: per-warp shared scratch of
+// `depth` entries.
+template <int K>
+__device__ __forceinline__ void emit_levels(const int32_t (&px)[K], const int32_t (&q)[K], int n,
+                                            int depth, unsigned long long* lq, int32_t* lp,
+                                            int32_t* out_px, int32_t* out_q)
+{
+    const int l = lane_id();
+    for (int k = l; k < depth; k += 32) {
+        lq[k] = 0;
+        lp[k] = -1;
+    }
+    __syncwarp();
+    const int32_t prev = __shfl_up_sync(kFull, px[K - 1], 1);
+    bool start[K];
+    int before = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        const int32_t left = j == 0 ? prev : px[j - 1];
+        start[j] = s < n && (s == 0 || px[j] != left);
+        const unsigned bal = __ballot_sync(kFull, start[j]);
+        before += __popc(bal & ((1u << l) - 1u));
+    }
+    int lvl = before - 1;
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        lvl += start[j] ? 1 : 0;
+        if (s < n && lvl < depth) {
+            atomicAdd(&lq[lvl], (unsigned long long)q[j]);
+            if (start[j]) lp[lvl] = px[j];
+        }
+    }
+    __syncwarp();
+    for (int k = l; k < depth; k += 32) {
+        out_px[k] = lp[k];
+        out_q[k] = (int32_t)min(lq[k], (unsigned long long)kMaxInt);
+    }
+    __syncwarp();
 }
 
 }  // namespace lob

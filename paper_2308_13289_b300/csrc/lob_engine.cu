@@ -79,24 +79,6 @@ __host__ __device__ constexpr int warp_smem_bytes(int chunk)
 template <int K>
 constexpr int max_threads() { return K >= 4 ? 256 : 512; }
 
-// Books whose two sides fit in registers (2 sides x 6 words x K per lane) stay
-// there for the whole stream; the largest capacity works in shared memory.
-template <int K>
-struct BookPolicy {
-    using type = RegBook<K>;
-};
-template <>
-struct BookPolicy<16> {
-    using type = SmemBook<16>;
-};
-
-__device__ __forceinline__ int64_t warp_sum64(int64_t x)
-{
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(kFull, x, d);
-    return x;
-}
-
 template <int K>
 __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
 {
@@ -161,6 +143,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
         int n_bid = a.counts[2 * b], n_ask = a.counts[2 * b + 1];
         Counters ctr{0, l};
         Tally tally;
+        NoObs obs;
         const int64_t tcount0 = ts.count;
         Book bk;
         if constexpr (!Book::kInRegisters) bk.base = image;
@@ -207,7 +190,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                     nb = mb[2 * i + 3];
                 }
                 apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
-                                 hb.z, hb.w, ts, tally);
+                                 hb.z, hb.w, ts, tally, obs);
             }
             __syncwarp();
             if (c + 2 < nchunks && l == 0) {
@@ -286,47 +269,15 @@ __global__ void k_levels(const char* __restrict__ state, const int32_t* __restri
         const char* side = state + (int64_t)b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
         const int32_t* px = reinterpret_cast<const int32_t*>(side + Geo<K>::PX);
         const int32_t* q = reinterpret_cast<const int32_t*>(side + Geo<K>::QTY);
-        const int n = counts[2 * b + x];
         int32_t vpx[K], vq[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             vpx[j] = px[l * K + j];
             vq[j] = q[l * K + j];
         }
-        for (int k = l; k < depth; k += 32) {
-            lq[w][k] = 0;
-            lp[w][k] = -1;
-        }
-        __syncwarp();
-        const int32_t prev = __shfl_up_sync(kFull, vpx[K - 1], 1);
-        bool start[K];
-        int before = 0;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int s = l * K + j;
-            const int32_t left = j == 0 ? prev : vpx[j - 1];
-            start[j] = s < n && (s == 0 || vpx[j] != left);
-            const unsigned bal = __ballot_sync(kFull, start[j]);
-            before += __popc(bal & ((1u << l) - 1u));
-        }
-        int lvl = before - 1;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const int s = l * K + j;
-            lvl += start[j] ? 1 : 0;
-            if (s < n && lvl < depth) {
-                atomicAdd(&lq[w][lvl], (unsigned long long)vq[j]);
-                if (start[j]) lp[w][lvl] = vpx[j];
-            }
-        }
-        __syncwarp();
-        int32_t* opx = (x == 0 ? bid_px : ask_px) + (int64_t)b * depth;
-        int32_t* oq = (x == 0 ? bid_qty : ask_qty) + (int64_t)b * depth;
-        for (int k = l; k < depth; k += 32) {
-            opx[k] = lp[w][k];
-            oq[k] = (int32_t)min(lq[w][k], (unsigned long long)kMaxInt);
-        }
-        __syncwarp();
+        emit_levels<K>(vpx, vq, counts[2 * b + x], depth, lq[w], lp[w],
+                       (x == 0 ? bid_px : ask_px) + (int64_t)b * depth,
+                       (x == 0 ? bid_qty : ask_qty) + (int64_t)b * depth);
     }
 }
 

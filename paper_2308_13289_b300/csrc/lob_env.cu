@@ -1,0 +1,569 @@
+// lob_env.cu -- execution-environment steps (Sec. 5) fused into one kernel.
+//
+// A warp owns one environment (= one book of a lob_ctx).  For each step it
+// stages the step's window of data messages in shared memory (bulk copy,
+// double-buffered across steps), replays them with the book kept on chip,
+// runs the synthetic execution agent (child sell orders, or the final cancel
+// and market sell), and writes the step's top levels, agent fills and VWAP
+// reward.  One launch can run many consecutive steps (the book never leaves
+// the SM between them); a single-step launch is what a CUDA graph captures.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+
+#include "../../include/lob.h"
+#include "lob_core.cuh"
+#include "lob_engine.h"
+
+using namespace lob;
+
+struct EnvStateDev {
+    int64_t submitted, executed, last_time;
+    int32_t id_counter, last_ask;
+    double p_init;
+};
+static_assert(sizeof(EnvStateDev) == 40, "env state layout");
+
+struct lob_env {
+    lob_ctx* book = nullptr;
+    lob_env_config_t cfg;
+    EnvStateDev* d_state = nullptr;
+    int chunk = 0;        // staged messages per step (msgs_per_step rounded up to 8)
+    int warps = 4;
+    int per_sm = 1;
+    int smem_per_cta = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+constexpr uint64_t kEnvWaitNs = 2000000000ull;
+constexpr int kLevelScratch = 64 * 8 + 64 * 4;
+
+struct EnvArgs {
+    const Msg* replay;
+    int64_t stride_env;
+    int32_t msgs_per_step, step0, n_run, n_envs;
+    const uint32_t* draws;
+    char* state;
+    int32_t* counts;
+    Trade* trades;
+    int64_t* tcounts;
+    int64_t* stats;
+    int32_t* status;
+    int32_t* queue;
+    int32_t cap, rule, trade_cap, chunk;
+    EnvStateDev* env;
+    int32_t n_steps, parent, agent_tid, depth, p_fallback, pad_;
+    double lambda;
+    float* reward;
+    int32_t *bid_px, *bid_qty, *ask_px, *ask_qty;
+    int64_t* fills;
+    uint64_t wait_ns;
+};
+
+template <int K>
+__host__ __device__ constexpr int env_warp_smem(int chunk)
+{
+    return ((Geo<K>::BOOK_BYTES + 2 * chunk * 32 + 16 + kLevelScratch) + 127) / 128 * 128;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
+{
+    using Book = typename BookPolicy<K>::type;
+    extern __shared__ __align__(128) char smem[];
+    const int l = lane_id();
+    const int warp = threadIdx.x >> 5;
+    const int W = blockDim.x >> 5;
+    const int chunk = a.chunk;
+    char* base = smem + warp * env_warp_smem<K>(chunk);
+    char* image = base;
+    char* msgbuf = base + Geo<K>::BOOK_BYTES;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk * 32);
+    unsigned long long* lq = reinterpret_cast<unsigned long long*>(msgbuf + 2 * chunk * 32 + 16);
+    int32_t* lp = reinterpret_cast<int32_t*>(lq + 64);
+    const int total_warps = gridDim.x * W;
+    const uint32_t bytes = (uint32_t)a.msgs_per_step * 32;
+
+    if (l == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+        fence_proxy_async();
+    }
+    __syncwarp();
+
+    uint32_t g = 0;
+    bool failed = false;
+    while (!failed) {
+        int item = 0;
+        if (l == 0) item = atomicAdd(&a.queue[0], 1);
+        item = __shfl_sync(kFull, item, 0);
+        if (item >= a.n_envs) break;
+        const int b = item;
+        char* gbook = a.state + (int64_t)b * Geo<K>::BOOK_BYTES;
+        const Msg* my = a.replay + (int64_t)b * a.stride_env;
+        if (l == 0) {
+            fence_proxy_async();
+            for (int c = 0; c < 2 && c < a.n_run; ++c) {
+                const uint32_t st = (g + c) & 1;
+                mbar_expect_tx(&bar[st], bytes + (c == 0 ? Geo<K>::BOOK_BYTES : 0));
+                if (c == 0) bulk_g2s(image, gbook, Geo<K>::BOOK_BYTES, &bar[st]);
+                bulk_g2s(msgbuf + st * chunk * 32,
+                         my + (int64_t)(a.step0 + c) * a.msgs_per_step, bytes, &bar[st]);
+            }
+        }
+        int n_bid = a.counts[2 * b], n_ask = a.counts[2 * b + 1];
+        EnvStateDev es = a.env[b];
+        Counters ctr{0, l};
+        Tally tally;
+        Book bk;
+        if constexpr (!Book::kInRegisters) bk.base = image;
+        int32_t c_kind[5] = {0, 0, 0, 0, 0};  // noop, invalid, limit, cancel, market (per lane)
+        int64_t q_limit = 0, q_market = 0, n_msgs = 0;
+        int64_t n_trades = 0, n_dropped = 0;
+        TradeSink ts{a.trades + (int64_t)b * a.trade_cap, 0, a.trade_cap};
+        for (int r = 0; r < a.n_run; ++r) {
+            const int t = a.step0 + r;
+            const uint32_t st = (g + r) & 1, par = ((g + r) >> 1) & 1;
+            if (!mbar_wait_bounded(&bar[st], par, a.wait_ns)) {
+                if (l == 0) atomicOr(a.status, LOB_STATUS_TIMEOUT);
+                const int last = min(r + 1, a.n_run - 1);
+                for (int d = r; d <= last; ++d)
+                    mbar_wait_bounded(&bar[(g + d) & 1], ((g + d) >> 1) & 1, a.wait_ns);
+                failed = true;
+                break;
+            }
+            if (r == 0) bk.from_image(image);
+            int4* mb = reinterpret_cast<int4*>(msgbuf + st * chunk * 32);
+            const int cnt = a.msgs_per_step;
+            for (int i = l; i < cnt; i += 32) {
+                const int4 h = mb[2 * i];
+                int kind = 0;
+                const int32_t op = classify(h.x, h.y, h.z, h.w, kind);
+                mb[2 * i].x = op;
+                c_kind[0] += kind == CTR_NOOP;
+                c_kind[1] += kind == CTR_INVALID;
+                c_kind[2] += kind == CTR_LIMIT;
+                c_kind[3] += kind == CTR_CANCEL;
+                c_kind[4] += kind == CTR_MARKET;
+                q_limit += kind == CTR_LIMIT ? h.w : 0;
+                q_market += kind == CTR_MARKET ? h.w : 0;
+            }
+            __syncwarp();
+            // 1. replay the step's data messages (trade log restarts each step)
+            ts.count = 0;
+            VwapObs obs;
+            obs.agent_tid = a.agent_tid;
+            const int64_t traded0 = tally.traded_qty;
+            int4 na = mb[0], nb = mb[1];
+            for (int i = 0; i < cnt; ++i) {
+                const int4 ha = na, hb = nb;
+                if (i + 1 < cnt) {
+                    na = mb[2 * i + 2];
+                    nb = mb[2 * i + 3];
+                }
+                apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
+                                 hb.z, hb.w, ts, tally, obs);
+            }
+            n_msgs += cnt;
+            if (cnt > 0) {
+                const int4 hl = mb[2 * (cnt - 1) + 1];
+                es.last_time = (int64_t)(((uint64_t)(uint32_t)hl.w << 32) | (uint32_t)hl.z);
+            }
+            const int32_t tlo = (int32_t)(uint32_t)(uint64_t)es.last_time;
+            const int32_t thi = (int32_t)(uint32_t)((uint64_t)es.last_time >> 32);
+            // 2. initial mid of the episode
+            if (t == 0) {
+                const int32_t bb = n_bid > 0 ? bk.template best_px<0>() : 0;
+                const int32_t ba = n_ask > 0 ? bk.template best_px<1>() : 0;
+                if (n_bid > 0 && n_ask > 0)
+                    es.p_init = __ddiv_rn(__dadd_rn((double)bb, (double)ba), 2.0);
+                else if (n_bid > 0)
+                    es.p_init = (double)bb;
+                else if (n_ask > 0)
+                    es.p_init = (double)ba;
+                else
+                    es.p_init = (double)a.p_fallback;
+            }
+            // 3. the agent's orders (every lane computes the same scalars)
+            if (t < a.n_steps - 1) {
+                if (n_ask > 0) es.last_ask = bk.template best_px<1>();
+                const int64_t remaining = (int64_t)a.parent - es.submitted;
+                const int64_t steps_left = (int64_t)a.n_steps - t;
+                const int64_t target =
+                    remaining > 0 ? (remaining + steps_left - 1) / steps_left : 0;
+                const uint32_t w = a.draws[(int64_t)r * a.n_envs + b];
+                const int nchild = (int)(w & 3u) + 1;
+                const int64_t base_q = target / nchild, extra = target % nchild;
+                for (int k = 0; k < nchild; ++k) {
+                    const int32_t q = (int32_t)(base_q + (k == 0 ? extra : 0));
+                    if (q <= 0) continue;
+                    const int32_t act = (int32_t)((w >> (2 + 3 * k)) & 7u);
+                    const int32_t oid = (int32_t)((1u << 30) + (uint32_t)es.id_counter);
+                    es.id_counter += 1;
+                    es.submitted += q;
+                    n_msgs += 1;
+                    if (act == 5) {
+                        if (l == 0) {
+                            c_kind[4] += 1;
+                            q_market += q;
+                        }
+                        apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, OP_MARKET_ASK, 0, q, oid,
+                                         a.agent_tid, tlo, thi, ts, tally, obs);
+                    } else {
+                        if (l == 0) {
+                            c_kind[2] += 1;
+                            q_limit += q;
+                        }
+                        const int32_t price = max(1, es.last_ask + act - 2);
+                        apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, OP_LIMIT_ASK, price, q,
+                                         oid, a.agent_tid, tlo, thi, ts, tally, obs);
+                    }
+                }
+            } else {
+                // last step: cancel the agent's resting orders in priority order
+                while (n_ask > 0) {
+                    SideVec<K> tmp;
+                    SideVec<K>& v = bk.template acquire<1>(tmp);
+                    int jj = -1;
+#pragma unroll
+                    for (int j = K - 1; j >= 0; --j)
+                        if (l * K + j < n_ask && v.tid[j] == a.agent_tid) jj = j;
+                    const unsigned hit = __ballot_sync(kFull, jj >= 0);
+                    if (hit == 0) break;
+                    const int L = __ffs(hit) - 1;
+                    const int j_hit = __shfl_sync(kFull, jj, L);
+                    const int p = L * K + j_hit;
+                    const int32_t q = __shfl_sync(kFull, pick<K>(v.q, j_hit), L);
+                    shift_out<K>(v.px, p, n_ask);
+                    shift_out<K>(v.q, p, n_ask);
+                    shift_out<K>(v.oid, p, n_ask);
+                    shift_out<K>(v.tid, p, n_ask);
+                    shift_out<K>(v.tlo, p, n_ask);
+                    shift_out<K>(v.thi, p, n_ask);
+                    bk.template release<1>(v, lane_touches<K>(p, n_ask - 1));
+                    if constexpr (!Book::kInRegisters) __syncwarp();
+                    n_ask -= 1;
+                    tally.cancel_hit += 1;
+                    tally.cancelled_qty += q;
+                    if (l == 0) c_kind[3] += 1;
+                    n_msgs += 1;
+                }
+                // ... then sell what is left at market
+                const int64_t left = (int64_t)a.parent - (es.executed + warp_sum64(obs.aq));
+                if (left > 0) {
+                    const int32_t oid = (int32_t)((1u << 30) + (uint32_t)es.id_counter);
+                    es.id_counter += 1;
+                    es.submitted += left;
+                    n_msgs += 1;
+                    if (l == 0) {
+                        c_kind[4] += 1;
+                        q_market += left;
+                    }
+                    apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, OP_MARKET_ASK, 0,
+                                     (int32_t)left, oid, a.agent_tid, tlo, thi, ts, tally, obs);
+                }
+            }
+            n_trades += ts.count;
+            n_dropped += max(ts.count - (int64_t)a.trade_cap, (int64_t)0);
+            // 4. fills and reward (eqs. rewardfunc, vwap), IEEE double
+            const int64_t sq = tally.traded_qty - traded0;
+            const int64_t spq = warp_sum64(obs.spq);
+            const int64_t aq = warp_sum64(obs.aq);
+            const int64_t apq = warp_sum64(obs.apq);
+            es.executed += aq;
+            const int64_t o = (int64_t)r * a.n_envs + b;
+            if (l == 0) {
+                double rew = 0.0;
+                if (sq > 0 && aq > 0) {
+                    const double vwap = __ddiv_rn((double)spq, (double)sq);
+                    const double adv = __dsub_rn((double)apq, __dmul_rn((double)aq, vwap));
+                    const double drift =
+                        __dmul_rn(a.lambda, __dmul_rn((double)aq, __dsub_rn(vwap, es.p_init)));
+                    rew = __dadd_rn(adv, drift);
+                }
+                a.reward[o] = (float)rew;
+                a.fills[2 * o] = aq;
+                a.fills[2 * o + 1] = apq;
+            }
+            // 5. top levels of both sides
+            {
+                SideVec<K> t0;
+                SideVec<K>& vb = bk.template acquire<0>(t0);
+                emit_levels<K>(vb.px, vb.q, n_bid, a.depth, lq, lp, a.bid_px + o * a.depth,
+                               a.bid_qty + o * a.depth);
+                SideVec<K> t1;
+                SideVec<K>& va = bk.template acquire<1>(t1);
+                emit_levels<K>(va.px, va.q, n_ask, a.depth, lq, lp, a.ask_px + o * a.depth,
+                               a.ask_qty + o * a.depth);
+            }
+            __syncwarp();
+            if (r + 2 < a.n_run && l == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&bar[st], bytes);
+                bulk_g2s(msgbuf + st * chunk * 32, my + (int64_t)(t + 2) * a.msgs_per_step, bytes,
+                         &bar[st]);
+            }
+        }
+        if (failed) break;
+        g += (uint32_t)a.n_run;
+        bk.to_image(image);
+        __syncwarp();
+        const int4* src = reinterpret_cast<const int4*>(image);
+        int4* dst = reinterpret_cast<int4*>(gbook);
+#pragma unroll 4
+        for (int i = l; i < Geo<K>::BOOK_BYTES / 16; i += 32) dst[i] = src[i];
+        // counters: data messages, agent orders and agent cancels all count
+        ctr.add(CTR_MSGS, n_msgs);
+        ctr.add(CTR_NOOP, __reduce_add_sync(kFull, (unsigned)c_kind[0]));
+        ctr.add(CTR_INVALID, __reduce_add_sync(kFull, (unsigned)c_kind[1]));
+        ctr.add(CTR_LIMIT, __reduce_add_sync(kFull, (unsigned)c_kind[2]));
+        ctr.add(CTR_CANCEL, __reduce_add_sync(kFull, (unsigned)c_kind[3]));
+        ctr.add(CTR_MARKET, __reduce_add_sync(kFull, (unsigned)c_kind[4]));
+        ctr.add(CTR_LIMIT_QTY, warp_sum64(q_limit));
+        ctr.add(CTR_MARKET_QTY, warp_sum64(q_market));
+        ctr.add(CTR_TRADES, n_trades);
+        ctr.add(CTR_TRADES_DROPPED, n_dropped);
+        ctr.add(CTR_TRADED_QTY, tally.traded_qty);
+        ctr.add(CTR_RESTED, tally.rested);
+        ctr.add(CTR_REJECTED, tally.rejected);
+        ctr.add(CTR_REJECTED_QTY, tally.rejected_qty);
+        ctr.add(CTR_EVICTED, tally.evicted);
+        ctr.add(CTR_EVICTED_QTY, tally.evicted_qty);
+        ctr.add(CTR_CANCEL_HIT, tally.cancel_hit);
+        ctr.add(CTR_CANCELLED_QTY, tally.cancelled_qty);
+        ctr.add(CTR_MARKET_DISCARDED_QTY, tally.discarded_qty);
+        const int64_t n_cancel = __shfl_sync(kFull, ctr.v, CTR_CANCEL);
+        const int64_t n_hit = __shfl_sync(kFull, ctr.v, CTR_CANCEL_HIT);
+        ctr.add(CTR_CANCEL_MISS, n_cancel - n_hit);
+        if (l < kNumCtr) a.stats[(int64_t)b * kNumCtr + l] += ctr.v;
+        if (l == 0) {
+            a.counts[2 * b] = n_bid;
+            a.counts[2 * b + 1] = n_ask;
+            a.tcounts[b] = ts.count;
+            a.env[b] = es;
+        }
+        __syncwarp();
+    }
+    if (l == 0) {
+        __threadfence();
+        const int done = atomicAdd(&a.queue[1], 1);
+        if (done == total_warps - 1) {
+            a.queue[0] = 0;
+            a.queue[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+const void* env_kernel(int K)
+{
+    switch (K) {
+    case 1: return reinterpret_cast<const void*>(&k_env<1>);
+    case 2: return reinterpret_cast<const void*>(&k_env<2>);
+    case 4: return reinterpret_cast<const void*>(&k_env<4>);
+    case 8: return reinterpret_cast<const void*>(&k_env<8>);
+    default: return reinterpret_cast<const void*>(&k_env<16>);
+    }
+}
+
+int env_smem(int K, int chunk)
+{
+    switch (K) {
+    case 1: return env_warp_smem<1>(chunk);
+    case 2: return env_warp_smem<2>(chunk);
+    case 4: return env_warp_smem<4>(chunk);
+    case 8: return env_warp_smem<8>(chunk);
+    default: return env_warp_smem<16>(chunk);
+    }
+}
+
+__global__ void k_env_reset(EnvStateDev* st, int32_t n, int32_t fallback)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    EnvStateDev s;
+    s.submitted = 0;
+    s.executed = 0;
+    s.last_time = 0;
+    s.id_counter = 0;
+    s.last_ask = fallback;
+    s.p_init = 0.0;
+    st[i] = s;
+}
+
+__global__ void k_env_state(const EnvStateDev* st, int32_t n, int64_t* out, double* p_init)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const EnvStateDev s = st[i];
+    if (out) {
+        out[5 * (int64_t)i + 0] = s.submitted;
+        out[5 * (int64_t)i + 1] = s.executed;
+        out[5 * (int64_t)i + 2] = s.id_counter;
+        out[5 * (int64_t)i + 3] = s.last_ask;
+        out[5 * (int64_t)i + 4] = s.last_time;
+    }
+    if (p_init) p_init[i] = s.p_init;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, void* stream)
+{
+    if (!out || !book || !cfg || cfg->n_steps < 1 || cfg->parent_qty < 0 || cfg->depth < 1 ||
+        cfg->depth > 64 || cfg->msgs_per_step < 1 || cfg->msgs_per_step > 1024 ||
+        cfg->p_init_fallback < 1) {
+        lob_set_error("lob_env_create: invalid argument");
+        return LOB_E_INVAL;
+    }
+    lob_env* e = new (std::nothrow) lob_env();
+    if (!e) {
+        lob_set_error("lob_env_create: host allocation failed");
+        return LOB_E_NOMEM;
+    }
+    e->book = book;
+    e->cfg = *cfg;
+    e->chunk = (cfg->msgs_per_step + 7) / 8 * 8;
+    const int K = book->K;
+    e->warps = K >= 8 ? 2 : 4;
+    e->smem_per_cta = env_smem(K, e->chunk) * e->warps;
+    int max_optin = 0;
+    cudaError_t err = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                             book->device);
+    if (err == cudaSuccess && e->smem_per_cta > max_optin) {
+        delete e;
+        lob_set_error("lob_env_create: %d messages per step do not fit in shared memory",
+                      cfg->msgs_per_step);
+        return LOB_E_INVAL;
+    }
+    if (err == cudaSuccess)
+        err = cudaFuncSetAttribute(env_kernel(K), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   e->smem_per_cta);
+    if (err == cudaSuccess)
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->per_sm, env_kernel(K),
+                                                            32 * e->warps, e->smem_per_cta);
+    if (err == cudaSuccess)
+        err = cudaMalloc(&e->d_state, sizeof(EnvStateDev) * (size_t)book->cfg.n_books);
+    if (err != cudaSuccess) {
+        delete e;
+        return lob_cuda_fail(err, "lob_env_create");
+    }
+    if (e->per_sm < 1) e->per_sm = 1;
+    int rc = lob_env_reset(e, stream);
+    if (rc != LOB_OK) {
+        lob_env_destroy(e);
+        return rc;
+    }
+    *out = e;
+    return LOB_OK;
+}
+
+int lob_env_destroy(lob_env* e)
+{
+    if (!e) return LOB_OK;
+    cudaError_t err = cudaSuccess;
+    if (e->d_state) {
+        err = cudaDeviceSynchronize();
+        cudaError_t e2 = cudaFree(e->d_state);
+        if (err == cudaSuccess) err = e2;
+    }
+    delete e;
+    return err == cudaSuccess ? LOB_OK : lob_cuda_fail(err, "lob_env_destroy");
+}
+
+int lob_env_reset(lob_env* e, void* stream)
+{
+    if (!e) {
+        lob_set_error("lob_env_reset: null environment");
+        return LOB_E_INVAL;
+    }
+    const int n = e->book->cfg.n_books;
+    k_env_reset<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(e->d_state, n,
+                                                                   e->cfg.p_init_fallback);
+    cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? LOB_OK : lob_cuda_fail(err, "lob_env_reset");
+}
+
+int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32_t step0,
+                int32_t n_run, const uint32_t* d_draws, float* d_reward, int32_t* d_bid_px,
+                int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty, int64_t* d_fills,
+                void* stream)
+{
+    if (!e || !d_replay || !d_draws || !d_reward || !d_bid_px || !d_bid_qty || !d_ask_px ||
+        !d_ask_qty || !d_fills || n_run < 1 || step0 < 0 || step0 + n_run > e->cfg.n_steps ||
+        stride_env < (int64_t)e->cfg.n_steps * e->cfg.msgs_per_step) {
+        lob_set_error("lob_env_run: invalid argument (step0=%d n_run=%d)", step0, n_run);
+        return LOB_E_INVAL;
+    }
+    if (((uintptr_t)d_replay & 15u) != 0) {
+        lob_set_error("lob_env_run: messages must be 16-byte aligned");
+        return LOB_E_INVAL;
+    }
+    lob_ctx* c = e->book;
+    EnvArgs a;
+    a.replay = reinterpret_cast<const Msg*>(d_replay);
+    a.stride_env = stride_env;
+    a.msgs_per_step = e->cfg.msgs_per_step;
+    a.step0 = step0;
+    a.n_run = n_run;
+    a.n_envs = c->cfg.n_books;
+    a.draws = d_draws;
+    a.state = c->d_state;
+    a.counts = c->d_counts;
+    a.trades = reinterpret_cast<Trade*>(c->d_trades);
+    a.tcounts = c->d_tcounts;
+    a.stats = c->d_stats;
+    a.status = c->d_status;
+    a.queue = c->d_queue;
+    a.cap = c->cfg.capacity;
+    a.rule = c->cfg.overflow_rule;
+    a.trade_cap = c->cfg.trade_capacity;
+    a.chunk = e->chunk;
+    a.env = e->d_state;
+    a.n_steps = e->cfg.n_steps;
+    a.parent = e->cfg.parent_qty;
+    a.agent_tid = e->cfg.agent_tid;
+    a.depth = e->cfg.depth;
+    a.p_fallback = e->cfg.p_init_fallback;
+    a.pad_ = 0;
+    a.lambda = e->cfg.lambda;
+    a.reward = d_reward;
+    a.bid_px = d_bid_px;
+    a.bid_qty = d_bid_qty;
+    a.ask_px = d_ask_px;
+    a.ask_qty = d_ask_qty;
+    a.fills = d_fills;
+    a.wait_ns = kEnvWaitNs;
+    const int W = e->warps;
+    int grid = (a.n_envs + W - 1) / W;
+    const int resident = c->num_sms * e->per_sm;
+    if (grid > resident) grid = resident;
+    void* args[] = {&a};
+    cudaError_t err = cudaLaunchKernel(env_kernel(c->K), dim3(grid), dim3(32 * W), args,
+                                       (size_t)e->smem_per_cta, (cudaStream_t)stream);
+    if (err != cudaSuccess) return lob_cuda_fail(err, "lob_env_run launch");
+    c->launches += 1;
+    e->launches += 1;
+    return LOB_OK;
+}
+
+int lob_env_get_state(lob_env* e, int64_t* d_state, double* d_p_init, void* stream)
+{
+    if (!e) {
+        lob_set_error("lob_env_get_state: null environment");
+        return LOB_E_INVAL;
+    }
+    const int n = e->book->cfg.n_books;
+    k_env_state<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(e->d_state, n, d_state,
+                                                                   d_p_init);
+    cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? LOB_OK : lob_cuda_fail(err, "lob_env_get_state");
+}
+
+}  // extern "C"
