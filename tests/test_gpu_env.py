@@ -97,16 +97,6 @@ def test_hand_worked_episode_on_gpu(eng):
     m = oracle.messages(rows)
     draws = np.array([[s["draw"]] for s in steps], dtype=np.uint32)
     for lam in (0.0, 0.5):
-        e, env, g = run_gpu(eng, m, 1, cfg["n_steps"], per, draws, cfg["capacity"], 64, lam,
-                            [cfg["n_steps"]], depth=cfg["depth"], parent=cfg["parent"])
-        oenv = oracle.EnvOracle(1, cfg["capacity"], 64, n_steps=cfg["n_steps"],
-                                parent_qty=cfg["parent"], agent_tid=AGENT, depth=cfg["depth"],
-                                p_init_fallback=cfg["p_init_fallback"], lam=lam)
-        oouts = []
-        for t in range(cfg["n_steps"]):
-            oouts.append(oenv.step(m[t * per:(t + 1) * per], np.array([0, per]), draws[t], t))
-        # agent tid 900 in the fixture
-        del e, env
         e = eng.Engine(1, cfg["capacity"], 64)
         env = eng.Env(e, n_steps=cfg["n_steps"], parent_qty=cfg["parent"], agent_tid=cfg["agent_tid"],
                       depth=cfg["depth"], p_init_fallback=cfg["p_init_fallback"], msgs_per_step=per,
