@@ -293,3 +293,64 @@ def decode_agent_draw(w: int):
     """(n_orders, [action codes]) from one packed agent draw."""
     n = (w & 3) + 1
     return n, [(w >> (2 + 3 * k)) & 7 for k in range(4)]
+
+
+class DeviceStreams:
+    """Resumable streams generated on the GPU (same definition as the host
+    side, bit for bit).  Memory is torch-allocated on the current device."""
+
+    def __init__(self, params: Params, n_books: int, stream_ids=None):
+        import torch
+        self.torch = torch
+        self.params = params
+        self.n = n_books
+        lib = cuda_lib()
+        self.lib = lib
+        dev = "cuda"
+        self.states = torch.zeros(n_books * STATE_BYTES, dtype=torch.uint8, device=dev)
+        self.pools = torch.zeros(n_books * params.pool_cap * POOL_ENTRY_BYTES, dtype=torch.uint8,
+                                 device=dev)
+        self.geo_px = torch.from_numpy(GEO_PX.view(np.int64)).to(dev)
+        self.geo_q = torch.from_numpy(GEO_Q.view(np.int64)).to(dev)
+        self.sid = None
+        if stream_ids is not None:
+            self.sid = torch.from_numpy(np.ascontiguousarray(stream_ids, dtype=np.uint64)
+                                        .view(np.int64)).to(dev)
+        rc = lib.lobgen_dev_init(ctypes.byref(params), n_books,
+                                 ctypes.c_void_p(self.sid.data_ptr()) if self.sid is not None
+                                 else None, ctypes.c_void_p(self.states.data_ptr()),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if rc != 0:
+            raise RuntimeError("lobgen_dev_init failed (%d)" % rc)
+
+    def advance(self, counts, ids=None, out=None):
+        """Draw counts[i] messages for book ids[i] (or i); returns (int32 [N, 8]
+        CUDA tensor, int64 CUDA offsets)."""
+        torch = self.torch
+        counts = torch.as_tensor(counts, dtype=torch.int64).cuda()
+        off = torch.zeros(counts.numel() + 1, dtype=torch.int64, device="cuda")
+        torch.cumsum(counts, 0, out=off[1:])
+        total = int(off[-1].item())
+        if out is None:
+            out = torch.empty((max(total, 1), 8), dtype=torch.int32, device="cuda")
+        idt = None if ids is None else torch.as_tensor(ids, dtype=torch.int32).cuda()
+        p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        rc = self.lib.lobgen_dev_advance(ctypes.byref(self.params), p(self.geo_px), p(self.geo_q),
+                                         counts.numel(), p(idt), p(self.states), p(self.pools),
+                                         p(counts), p(off), p(out),
+                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if rc != 0:
+            raise RuntimeError("lobgen_dev_advance failed (%d)" % rc)
+        return out[:total], off
+
+
+def agent_draws_device(seed: int, n_envs: int, n_steps: int, step0: int = 0):
+    """[n_steps, n_envs] agent draws generated on the GPU (int32 view of uint32)."""
+    import torch
+    out = torch.empty((n_steps, n_envs), dtype=torch.int32, device="cuda")
+    rc = cuda_lib().lobgen_dev_agent_draws(seed & ((1 << 64) - 1), n_envs, step0, n_steps,
+                                           ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc != 0:
+        raise RuntimeError("lobgen_dev_agent_draws failed (%d)" % rc)
+    return out
