@@ -149,6 +149,11 @@ int lob_destroy(lob_ctx* ctx);
 /* Empty every book, clear the trade logs, counters and status word. */
 int lob_reset(lob_ctx* ctx, void* stream);
 
+/* Empty the books d_book_ids[0 .. n) (int32, device) and clear their trade
+ * logs and counters; other books are untouched (a serving slot handed to a
+ * new episode).  Ids outside [0, n_books) are skipped (LOB_STATUS_BAD_BOOK). */
+int lob_reset_books(lob_ctx* ctx, const int32_t* d_book_ids, int32_t n, void* stream);
+
 /* -------------------------------------------------------------- processing */
 
 /* Apply message segments to books (Sec. 4.2 dispatch; Sec. 4.1 add, cancel,

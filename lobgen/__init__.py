@@ -210,6 +210,7 @@ def cuda_lib():
         vp = ctypes.c_void_p
         lib.lobgen_dev_init.argtypes = [vp, ctypes.c_int32, vp, vp, vp]
         lib.lobgen_dev_advance.argtypes = [vp, vp, vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp]
+        lib.lobgen_dev_init_ids.argtypes = [vp, ctypes.c_int32, vp, vp, vp, vp]
         lib.lobgen_dev_agent_draws.argtypes = [ctypes.c_uint64, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.c_int32, vp, vp]
         _cuda = lib
@@ -322,6 +323,19 @@ class DeviceStreams:
                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         if rc != 0:
             raise RuntimeError("lobgen_dev_init failed (%d)" % rc)
+
+    def restart(self, ids, stream_ids):
+        """Books ids[i] restart as streams stream_ids[i] (device tensors or arrays)."""
+        torch = self.torch
+        idt = torch.as_tensor(np.asarray(ids, dtype=np.int32)).cuda()
+        sid = torch.as_tensor(np.asarray(stream_ids, dtype=np.uint64).view(np.int64)).cuda()
+        rc = self.lib.lobgen_dev_init_ids(ctypes.byref(self.params), idt.numel(),
+                                          ctypes.c_void_p(idt.data_ptr()),
+                                          ctypes.c_void_p(sid.data_ptr()),
+                                          ctypes.c_void_p(self.states.data_ptr()),
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        if rc != 0:
+            raise RuntimeError("lobgen_dev_init_ids failed (%d)" % rc)
 
     def advance(self, counts, ids=None, out=None):
         """Draw counts[i] messages for book ids[i] (or i); returns (int32 [N, 8]

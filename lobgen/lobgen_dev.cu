@@ -21,6 +21,17 @@ __global__ void k_init(lobgen_params_t p, int32_t n_books, const uint64_t* strea
     states[b] = s;
 }
 
+// State of book ids[i] restarts as stream stream_ids[i].
+__global__ void k_init_ids(lobgen_params_t p, int32_t n, const int32_t* ids,
+                           const uint64_t* stream_ids, lobgen_state_t* states)
+{
+    int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    lobgen_state_t s;
+    lg_init_state(&p, stream_ids[i], &s);
+    states[ids[i]] = s;
+}
+
 // Book b (= ids[i] when ids is given) appends counts[i] messages at
 // out + out_offsets[i].
 __global__ void k_advance(lobgen_params_t p, const uint64_t* __restrict__ geo_px,
@@ -60,6 +71,16 @@ int lobgen_dev_init(const lobgen_params_t* p, int32_t n_books, const uint64_t* d
     if (n_books == 0) return 0;
     k_init<<<(n_books + 127) / 128, 128, 0, (cudaStream_t)stream>>>(*p, n_books, d_stream_ids,
                                                                      d_states);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int lobgen_dev_init_ids(const lobgen_params_t* p, int32_t n, const int32_t* d_ids,
+                        const uint64_t* d_stream_ids, lobgen_state_t* d_states, void* stream)
+{
+    if (!p || !d_ids || !d_stream_ids || !d_states || n < 0) return -1;
+    if (n == 0) return 0;
+    k_init_ids<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(*p, n, d_ids, d_stream_ids,
+                                                                 d_states);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

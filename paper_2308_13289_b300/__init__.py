@@ -82,6 +82,11 @@ def lob_reset(h, stream=None):
     check(lib().lob_reset(h, _stream(stream)), "lob_reset")
 
 
+def lob_reset_books(h, book_ids, stream=None):
+    check(lib().lob_reset_books(h, _ptr(book_ids), book_ids.numel(), _stream(stream)),
+          "lob_reset_books")
+
+
 def lob_process_batch(h, msgs, offsets, book_ids=None, n_active=None, stream=None):
     n = (offsets.numel() - 1) if n_active is None else n_active
     check(lib().lob_process_batch(h, _ptr(msgs), _ptr(offsets), _ptr(book_ids), n,
@@ -198,6 +203,9 @@ class Engine:
 
     def reset(self):
         lob_reset(self.h, self.stream)
+
+    def reset_books(self, book_ids):
+        lob_reset_books(self.h, book_ids, self.stream)
 
     def process_batch(self, msgs, offsets, book_ids=None):
         lob_process_batch(self.h, msgs, offsets, book_ids, stream=self.stream)

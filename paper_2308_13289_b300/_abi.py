@@ -27,6 +27,7 @@ SIGNATURES = {
     "lob_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(LobConfig), vp]),
     "lob_destroy": (ctypes.c_int, [vp]),
     "lob_reset": (ctypes.c_int, [vp, vp]),
+    "lob_reset_books": (ctypes.c_int, [vp, vp, i32, vp]),
     "lob_process_batch": (ctypes.c_int, [vp, vp, vp, vp, i32, vp]),
     "lob_inject_orders": (ctypes.c_int, [vp, vp, vp, vp, i32, vp]),
     "lob_clear_trades": (ctypes.c_int, [vp, vp]),

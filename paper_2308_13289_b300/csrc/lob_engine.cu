@@ -347,6 +347,22 @@ __global__ void k_set_book(char* state, int32_t* counts, int32_t n_books, int32_
     if (l == 0) counts[bx] = n;
 }
 
+__global__ void k_reset_books(const int32_t* __restrict__ ids, int32_t n, int32_t n_books,
+                              int32_t* counts, int64_t* tcounts, int64_t* stats, int32_t* status)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t b = ids[i];
+    if (b < 0 || b >= n_books) {
+        atomicOr(status, LOB_STATUS_BAD_BOOK);
+        return;
+    }
+    counts[2 * b] = 0;
+    counts[2 * b + 1] = 0;
+    tcounts[b] = 0;
+    for (int k = 0; k < kNumCtr; ++k) stats[(int64_t)b * kNumCtr + k] = 0;
+}
+
 __global__ void k_get_trades(const Trade* __restrict__ log, const int64_t* __restrict__ tcounts,
                              int32_t n_books, int32_t cap, Trade* out)
 {
@@ -589,6 +605,21 @@ int lob_reset(lob_ctx* c, void* stream)
         e = cudaMemsetAsync(c->d_stats, 0, (size_t)nb * kNumCtr * sizeof(int64_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 64, s);
     if (e != cudaSuccess) return lob_cuda_fail(e, "lob_reset");
+    return LOB_OK;
+}
+
+int lob_reset_books(lob_ctx* c, const int32_t* d_book_ids, int32_t n, void* stream)
+{
+    if (!c || n < 0 || (n > 0 && !d_book_ids)) {
+        lob_set_error("lob_reset_books: invalid argument");
+        return LOB_E_INVAL;
+    }
+    if (n == 0) return LOB_OK;
+    k_reset_books<<<(n + 127) / 128, 128, 0, (cudaStream_t)stream>>>(
+        d_book_ids, n, c->cfg.n_books, c->d_counts, c->d_tcounts, c->d_stats, c->d_status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_reset_books");
+    c->launches += 1;
     return LOB_OK;
 }
 
