@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--oracle-books", type=int, default=256,
                     help="books of the CPU-baseline sample (full streams)")
     ap.add_argument("--launch", default="", help="warps,chunk,ctas_per_sm override")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the uneven / RL-environment / serving workloads")
+    ap.add_argument("--serving-window", type=float, default=2.0,
+                    help="seconds of Poisson arrivals in the serving workload")
     return ap.parse_args()
 
 
@@ -317,6 +321,16 @@ def run_engine(args):
             "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": int(alg_bytes),
             "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
 
+    extras = None
+    if not args.no_extras and args.workload == "replay_1024x100k":
+        e.close()
+        del d_msgs
+        torch.cuda.empty_cache()
+        extras = {"uneven_4096_lognormal": run_uneven(args, rank),
+                  "rl_exec_8192x400": run_rl(args, rank),
+                  "serving_mix": run_serving(args, rank)}
+        e = eng.Engine(1, cap, 1)
+
     if rank == 0:
         value = total_msgs * world / (ms_step / 1e3)
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -332,12 +346,196 @@ def run_engine(args):
                 "plain": plain, "plain_graph": plain_graph,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "parity": parity,
-                "device_status": status}
+                "device_status": status, "workloads": extras}
         print(json.dumps(line))
     e.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_uneven(args, rank):
+    """4,096 books with lognormal message counts in ONE persistent launch whose
+    work queue hands out books in natural order or longest first."""
+    import torch
+
+    import lobgen
+    import oracle
+    import paper_2308_13289_b300 as eng
+    w = lobgen.WORKLOADS["uneven_4096_lognormal"]
+    n = w["n_books"]
+    counts = lobgen.lognormal_counts(n, w["seed"])
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    ids = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
+    tcap = trade_capacity_for(counts)
+    res = {"n_books": n, "messages": int(counts.sum()), "count_min": int(counts.min()),
+           "count_max": int(counts.max()), "count_mean": float(counts.mean())}
+    for order in ("natural", "longest_first"):
+        perm = np.arange(n) if order == "natural" else np.argsort(-counts, kind="stable")
+        gen = lobgen.DeviceStreams(params, n, stream_ids=ids)
+        dm, doff = gen.advance(counts[perm], ids=perm.astype(np.int32))
+        d_ids = torch.from_numpy(perm.astype(np.int32)).cuda()
+        e = eng.Engine(n, w["capacity"], tcap)
+        times = []
+        for i in range(args.warmup + args.steps):
+            e.reset()
+            a, b = _events()
+            a.record()
+            e.process_batch(dm, doff, d_ids)
+            b.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+        ms = float(np.mean(times))
+        res[order] = {"ms_per_step": round(ms, 4), "msgs_per_s": round(res["messages"] / ms * 1e3, 1)}
+        if order == "longest_first" and rank == 0:
+            # parity on a sample of books (oracle replays their own streams)
+            sample = np.array(sorted(set([0, 1, n - 1] + list(perm[:3]) + list(perm[-3:]))))
+            hm, hoff = lobgen.generate(params, counts[sample], stream_ids=ids[sample])
+            o = oracle.Oracle(len(sample), w["capacity"], tcap)
+            o.process(hm, hoff)
+            bk = e.book()
+            ok = all(np.array_equal(bk[k][sample].cpu().numpy(), v) for k, v in o.book().items())
+            ctr, st = e.stats()
+            ok &= np.array_equal(ctr[sample].cpu().numpy(), o.counters())
+            res["parity"] = {"books_checked": int(len(sample)), "bit_exact": bool(ok),
+                             "device_status": int(st.item())}
+        e.close()
+        del dm, doff, gen
+    return res
+
+
+def run_rl(args, rank):
+    """8,192 execution environments x 400 steps x 100 data messages: one launch
+    per step, the same 400 launches replayed from a CUDA graph, and one
+    persistent launch for the whole episode."""
+    import torch
+
+    import lobgen
+    import oracle
+    import paper_2308_13289_b300 as eng
+    w = lobgen.WORKLOADS["rl_exec_8192x400"]
+    n, steps, per = w["n_books"], w["steps"], w["msgs_per_step"]
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    ids = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
+    gen = lobgen.DeviceStreams(params, n, stream_ids=ids)
+    dm, _ = gen.advance([steps * per] * n)
+    del gen
+    draws = lobgen.agent_draws_device(w["seed"] + 1, n, steps)
+    e = eng.Engine(n, w["capacity"], 4096)
+    env = eng.Env(e, n_steps=steps, msgs_per_step=per)
+    out = env.outputs(steps)
+    stride = steps * per
+
+    def per_step():
+        e.reset()
+        env.reset()
+        for t in range(steps):
+            env.run(dm, stride, t, 1, draws[t:t + 1], out, row0=t)
+
+    def persistent():
+        e.reset()
+        env.reset()
+        env.run(dm, stride, 0, steps, draws, out)
+
+    def snapshot():
+        torch.cuda.synchronize()
+        st, p0 = env.state()
+        return [v.clone() for v in out.values()] + [st, p0] + list(e.book().values())
+
+    res = {"n_envs": n, "steps": steps, "msgs_per_step": per}
+    ref = None
+    forms = {}
+    for name, fn in (("per_step_launches", per_step), ("persistent_episode", persistent)):
+        times = []
+        for i in range(max(1, args.warmup) + max(2, args.steps // 3)):
+            a, b = _events()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if i >= max(1, args.warmup):
+                times.append(a.elapsed_time(b))
+        forms[name] = float(np.mean(times))
+        snap = snapshot()
+        if ref is None:
+            ref = snap
+        else:
+            res["persistent_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snap))
+    # CUDA graph of the per-step form
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s2):
+        with torch.cuda.graph(g, stream=s2):
+            per_step()
+    torch.cuda.current_stream().wait_stream(s2)
+    times = []
+    for i in range(max(1, args.warmup) + max(2, args.steps // 3)):
+        a, b = _events()
+        a.record()
+        g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        if i >= max(1, args.warmup):
+            times.append(a.elapsed_time(b))
+    forms["graph_per_step"] = float(np.mean(times))
+    res["graph_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snapshot()))
+    del g
+    for name, ms in forms.items():
+        res[name] = {"ms_per_episode": round(ms, 3),
+                     "env_steps_per_s": round(n * steps / ms * 1e3, 1),
+                     "data_msgs_per_s": round(n * steps * per / ms * 1e3, 1),
+                     "launches": 1 if name == "persistent_episode" else steps}
+    if rank == 0:
+        sample = np.array([0, 1, 2, n // 2, n - 1])
+        hm, hoff = lobgen.generate(params, [steps * per] * len(sample), stream_ids=ids[sample])
+        hd = lobgen.agent_draws(w["seed"] + 1, n, steps)[:, sample]
+        oenv = oracle.EnvOracle(len(sample), w["capacity"], 4096, n_steps=steps)
+        rows = hm.reshape(len(sample), steps, per)
+        ok = True
+        rew = out["reward"].cpu().numpy()
+        fills = out["fills"].cpu().numpy()
+        lvb = out["bid_px"].cpu().numpy()
+        for t in range(steps):
+            stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
+            r_, lv, f_ = oenv.step(stp, np.arange(0, len(sample) * per + 1, per), hd[t], t)
+            ok &= rew[t, sample].tobytes() == r_.tobytes()
+            ok &= np.array_equal(fills[t, sample], f_)
+            ok &= np.array_equal(lvb[t, sample], lv[0])
+        res["parity"] = {"envs_checked": int(len(sample)), "steps_checked": steps,
+                         "bit_exact": bool(ok)}
+    env.close()
+    e.close()
+    del dm, out
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_serving(args, rank):
+    """Poisson arrivals (2,000 episodes/s) of episodes with capacity 100/250/500,
+    200..2,000 steps and 100..500 messages per step, served by continuous
+    batching with admission by HBM footprint."""
+    import lobgen
+    from paper_2308_13289_b300.serve import Server, sample_episodes
+    w = lobgen.WORKLOADS["serving_mix"]
+    eps = sample_episodes(w["rate"], args.serving_window, w["seed"] + rank, w["capacities"],
+                          w["steps"], w["msgs_per_step"])
+    srv = Server(capacities=w["capacities"], seed=w["seed"])
+    rep = srv.run(eps, clock="wall")
+    q = rep.pop("queue")
+    rep["queue_samples"] = [(round(t, 3), n) for t, n in q[::max(1, len(q) // 20)]]
+    rep["offered_msgs_per_s"] = round(sum(e.n_steps * e.msgs_per_step for e in eps)
+                                      / args.serving_window, 1)
+    rep["window_s"] = args.serving_window
+    for k in ("wall_s", "steps_per_s", "msgs_per_s", "p50_step_ms", "p99_step_ms"):
+        rep[k] = round(rep[k], 4)
+    return rep
 
 
 def eng_book_bytes(cap):
