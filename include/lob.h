@@ -173,6 +173,14 @@ int lob_reset_books(lob_ctx* ctx, const int32_t* d_book_ids, int32_t n, void* st
 int lob_process_batch(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_offsets,
                       const int32_t* d_book_ids, int32_t n_active, void* stream);
 
+/* Same as lob_process_batch, but segment i is d_msgs[d_starts[i] ..
+ * d_starts[i] + d_counts[i]) (int64 each, device), so the segments may lie
+ * anywhere in d_msgs -- e.g. the current step window of each of many resident
+ * episodes whose messages are pre-loaded.  d_book_ids is required. */
+int lob_process_segments(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_starts,
+                         const int64_t* d_counts, const int32_t* d_book_ids, int32_t n_active,
+                         void* stream);
+
 /* Same as lob_process_batch, but the trades are appended to the log of the
  * previous call (for orders injected after a replay, Sec. 5.1.3 step 4). */
 int lob_inject_orders(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_offsets,

@@ -54,7 +54,8 @@ constexpr uint64_t kWaitNs = 2000000000ull;  // bounded wait for a staged chunk:
 
 struct ProcArgs {
     const Msg* msgs;
-    const int64_t* offsets;
+    const int64_t* offsets;  // [n_items+1] boundaries, or starts when `counts_in` is set
+    const int64_t* counts_in;
     const int32_t* book_ids;
     int32_t n_items;
     int32_t n_books;
@@ -114,7 +115,8 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
             if (l == 0) atomicOr(a.status, LOB_STATUS_BAD_BOOK);
             continue;
         }
-        const int64_t lo = a.offsets[item], hi = a.offsets[item + 1];
+        const int64_t lo = a.offsets[item];
+        const int64_t hi = a.counts_in ? lo + a.counts_in[item] : a.offsets[item + 1];
         if (hi < lo) {
             if (l == 0) atomicOr(a.status, LOB_STATUS_BAD_SEGMENT);
             continue;
@@ -423,12 +425,13 @@ int lob_book_bytes(int K) { return 48 * 32 * K; }
 
 int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
                        const int32_t* d_book_ids, int32_t n_active, int append,
-                       cudaStream_t stream)
+                       cudaStream_t stream, const int64_t* d_counts)
 {
     if (n_active == 0) return LOB_OK;
     ProcArgs a;
     a.msgs = reinterpret_cast<const Msg*>(d_msgs);
     a.offsets = d_offsets;
+    a.counts_in = d_counts;
     a.book_ids = d_book_ids;
     a.n_items = n_active;
     a.n_books = c->cfg.n_books;
@@ -658,7 +661,22 @@ int lob_process_batch(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offs
     if (rc != LOB_OK) return rc;
     const int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
     return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, append,
-                              (cudaStream_t)stream);
+                              (cudaStream_t)stream, nullptr);
+}
+
+int lob_process_segments(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_starts,
+                         const int64_t* d_counts, const int32_t* d_book_ids, int32_t n_active,
+                         void* stream)
+{
+    int rc = check_batch(c, d_msgs, d_starts, d_book_ids, n_active, "lob_process_segments");
+    if (rc != LOB_OK) return rc;
+    if (n_active > 0 && (!d_counts || !d_book_ids)) {
+        lob_set_error("lob_process_segments: null counts or book ids");
+        return LOB_E_INVAL;
+    }
+    const int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
+    return lob_launch_process(c, d_msgs, d_starts, d_book_ids, n_active, append,
+                              (cudaStream_t)stream, d_counts);
 }
 
 int lob_inject_orders(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
@@ -667,7 +685,7 @@ int lob_inject_orders(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offs
     int rc = check_batch(c, d_msgs, d_offsets, d_book_ids, n_active, "lob_inject_orders");
     if (rc != LOB_OK) return rc;
     return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, 1,
-                              (cudaStream_t)stream);
+                              (cudaStream_t)stream, nullptr);
 }
 
 int lob_clear_trades(lob_ctx* c, void* stream)
@@ -931,6 +949,7 @@ extern "C" int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t
     ProcArgs a;
     a.msgs = reinterpret_cast<const Msg*>(d_msgs);
     a.offsets = d_offsets;
+    a.counts_in = nullptr;
     a.book_ids = nullptr;
     a.n_items = n_books;
     a.n_books = n_books;

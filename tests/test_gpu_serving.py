@@ -32,15 +32,15 @@ def _clone(eps):
 def test_alone_equals_mix_and_oracle():
     from paper_2308_13289_b300.serve import Server
     eps = _mix()
-    srv = Server(capacities=(7, 100, 250), trade_capacity=512, max_msgs=64, max_slots=6,
-                 collect=True, seed=77)
+    srv = Server(capacities=(7, 100, 250), trade_capacity=512, max_slots=6, collect=True,
+                 seed=77)
     rep = srv.run(_clone(eps), clock="virtual")
     assert rep["episode_steps"] == sum(e.n_steps for e in eps)
     assert rep["max_queue"] > 0, "the mix should make episodes wait for slots"
     assert rep["max_active"] > 6, "several capacity classes should run at once"
     for ep in eps[:12]:
-        alone = Server(capacities=(ep.capacity,), trade_capacity=512, max_msgs=64, max_slots=1,
-                       collect=True, seed=77)
+        alone = Server(capacities=(ep.capacity,), trade_capacity=512, max_slots=1, collect=True,
+                       seed=77)
         import copy
         e1 = copy.copy(ep)
         e1.arrival = 0.0
@@ -65,14 +65,32 @@ def test_alone_equals_mix_and_oracle():
             assert np.array_equal(v[0], srv.final_books[ep.id][k]), (ep.id, k)
 
 
+def test_process_segments_equals_process_batch():
+    """Scattered (start, count) segments give the contiguous-offsets result."""
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    from engine_harness import assert_same, gpu_outputs
+    n, per = 10, 700
+    m, off = lobgen.generate(lobgen.make_params(11), [per] * n)
+    d = eng.messages_to_device(m)
+    a = eng.Engine(n, 100, 2048)
+    a.process_batch(d, torch.from_numpy(off).cuda())
+    b = eng.Engine(n, 100, 2048)
+    perm = np.random.default_rng(1).permutation(n).astype(np.int32)
+    starts = torch.from_numpy(off[perm]).cuda()
+    counts = torch.full((n,), per, dtype=torch.int64, device="cuda")
+    eng.lob_process_segments(b.h, d, starts, counts, torch.from_numpy(perm).cuda())
+    assert_same(gpu_outputs(b), gpu_outputs(a))
+
+
 def test_admission_respects_hbm_budget():
     from paper_2308_13289_b300.serve import Server, footprint_bytes
     eps = _mix(24, seed=9)
     for e in eps:
         e.capacity = 100
-    fp = footprint_bytes(100, 256, 64, lobgen.DEFAULT_POOL)
-    srv = Server(capacities=(100,), hbm_budget=5 * fp, trade_capacity=256, max_msgs=64,
-                 max_slots=64, seed=3)
+    fp = footprint_bytes(100, 256)
+    srv = Server(capacities=(100,), hbm_budget=5 * fp, trade_capacity=256, max_slots=64, seed=3)
     rep = srv.run(eps, clock="virtual")
     assert rep["max_active"] <= 5
     assert rep["max_hbm_bytes_admitted"] <= 5 * fp
