@@ -410,7 +410,7 @@ def run_uneven(args, rank):
     return res
 
 
-def run_rl(args, rank):
+def run_rl(args, rank, name="rl_exec_8192x400"):
     """8,192 execution environments x 400 steps x 100 data messages: one launch
     per step, the same 400 launches replayed from a CUDA graph, and one
     persistent launch for the whole episode."""
@@ -419,7 +419,7 @@ def run_rl(args, rank):
     import lobgen
     import oracle
     import paper_2308_13289_b300 as eng
-    w = lobgen.WORKLOADS["rl_exec_8192x400"]
+    w = lobgen.WORKLOADS[name]
     n, steps, per = w["n_books"], w["steps"], w["msgs_per_step"]
     params = lobgen.make_params(w["seed"], w["mid_walk"])
     ids = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
@@ -681,10 +681,36 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_single(args):
+    """One non-headline workload on its own, printed as its own JSON line."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2308_13289_b300 import build as eng_build
+    eng_build.build()
+    wl = args.workload
+    if wl.startswith("rl_exec"):
+        r = run_rl(args, rank, wl)
+        value, unit = r["persistent_episode"]["env_steps_per_s"], "env-steps/s"
+    elif wl.startswith("uneven"):
+        r = run_uneven(args, rank)
+        value, unit = r["natural"]["msgs_per_s"], UNIT
+    else:
+        r = run_serving(args, rank)
+        value, unit = r["steps_per_s"], "episode-steps/s"
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": unit, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": DATA,
+                          "config": {"workload": wl}, "result": r}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith(("rl_exec", "uneven", "serving")):
+        run_single(args)
     else:
         run_engine(args)
 

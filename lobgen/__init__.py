@@ -137,6 +137,9 @@ WORKLOADS = {
     # 8,192 RL envs x 400 steps x 100 replay messages (+ 1..4 agent orders), capacity 100
     "rl_exec_8192x400": dict(n_books=8192, steps=400, msgs_per_step=100, capacity=100,
                              mid_walk="pm1", seed=20230828),
+    # profiling case: the RL workload cut to 40 steps
+    "rl_exec_8192x40": dict(n_books=8192, steps=40, msgs_per_step=100, capacity=100,
+                            mid_walk="pm1", seed=20230828),
     # serving mix: Poisson 2,000 episodes/s, capacity {100,250,500}, 200..2,000 steps,
     # 100..500 messages per step
     "serving_mix": dict(rate=2000.0, capacities=(100, 250, 500), steps=(200, 2000),

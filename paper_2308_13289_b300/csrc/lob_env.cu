@@ -40,6 +40,7 @@ namespace {
 
 constexpr uint64_t kEnvWaitNs = 2000000000ull;
 constexpr int kLevelScratch = 64 * 8 + 64 * 4;
+constexpr int kAgentRecs = 8;  // staged agent orders of one step (at most 4 + 1)
 
 struct EnvArgs {
     const Msg* replay;
@@ -66,7 +67,8 @@ struct EnvArgs {
 template <int K>
 __host__ __device__ constexpr int env_warp_smem(int chunk)
 {
-    return ((Geo<K>::BOOK_BYTES + 2 * chunk * 32 + 16 + kLevelScratch) + 127) / 128 * 128;
+    return ((Geo<K>::BOOK_BYTES + 2 * chunk * 32 + 16 + kLevelScratch + kAgentRecs * 32) + 127) /
+           128 * 128;
 }
 
 template <int K>
@@ -84,6 +86,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
     uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk * 32);
     unsigned long long* lq = reinterpret_cast<unsigned long long*>(msgbuf + 2 * chunk * 32 + 16);
     int32_t* lp = reinterpret_cast<int32_t*>(lq + 64);
+    int4* agent_buf = reinterpret_cast<int4*>(lp + 64);
     const int total_warps = gridDim.x * W;
     const uint32_t bytes = (uint32_t)a.msgs_per_step * 32;
 
@@ -158,113 +161,117 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
             VwapObs obs;
             obs.agent_tid = a.agent_tid;
             const int64_t traded0 = tally.traded_qty;
-            int4 na = mb[0], nb = mb[1];
-            for (int i = 0; i < cnt; ++i) {
-                const int4 ha = na, hb = nb;
-                if (i + 1 < cnt) {
-                    na = mb[2 * i + 2];
-                    nb = mb[2 * i + 3];
-                }
-                apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
-                                 hb.z, hb.w, ts, tally, obs);
-            }
-            n_msgs += cnt;
+            // last data time of the window (agent orders carry it)
             if (cnt > 0) {
                 const int4 hl = mb[2 * (cnt - 1) + 1];
                 es.last_time = (int64_t)(((uint64_t)(uint32_t)hl.w << 32) | (uint32_t)hl.z);
             }
-            const int32_t tlo = (int32_t)(uint32_t)(uint64_t)es.last_time;
-            const int32_t thi = (int32_t)(uint32_t)((uint64_t)es.last_time >> 32);
-            // 2. initial mid of the episode
-            if (t == 0) {
-                const int32_t bb = n_bid > 0 ? bk.template best_px<0>() : 0;
-                const int32_t ba = n_ask > 0 ? bk.template best_px<1>() : 0;
-                if (n_bid > 0 && n_ask > 0)
-                    es.p_init = __ddiv_rn(__dadd_rn((double)bb, (double)ba), 2.0);
-                else if (n_bid > 0)
-                    es.p_init = (double)bb;
-                else if (n_ask > 0)
-                    es.p_init = (double)ba;
-                else
-                    es.p_init = (double)a.p_fallback;
-            }
-            // 3. the agent's orders (every lane computes the same scalars)
-            if (t < a.n_steps - 1) {
-                if (n_ask > 0) es.last_ask = bk.template best_px<1>();
-                const int64_t remaining = (int64_t)a.parent - es.submitted;
-                const int64_t steps_left = (int64_t)a.n_steps - t;
-                const int64_t target =
-                    remaining > 0 ? (remaining + steps_left - 1) / steps_left : 0;
-                const uint32_t w = a.draws[(int64_t)r * a.n_envs + b];
-                const int nchild = (int)(w & 3u) + 1;
-                const int64_t base_q = target / nchild, extra = target % nchild;
-                for (int k = 0; k < nchild; ++k) {
-                    const int32_t q = (int32_t)(base_q + (k == 0 ? extra : 0));
-                    if (q <= 0) continue;
-                    const int32_t act = (int32_t)((w >> (2 + 3 * k)) & 7u);
-                    const int32_t oid = (int32_t)((1u << 30) + (uint32_t)es.id_counter);
-                    es.id_counter += 1;
-                    es.submitted += q;
-                    n_msgs += 1;
-                    if (act == 5) {
+            n_msgs += cnt;
+            // phase 0: the window's data messages; phase 1: the agent's orders,
+            // staged as records and run through the same (not unrolled) loop
+#pragma unroll 1
+            for (int phase = 0; phase < 2; ++phase) {
+                const int4* src = mb;
+                int count = cnt;
+                if (phase == 1) {
+                    src = agent_buf;
+                    count = 0;
+                    const int32_t tlo = (int32_t)(uint32_t)(uint64_t)es.last_time;
+                    const int32_t thi = (int32_t)(uint32_t)((uint64_t)es.last_time >> 32);
+                    auto stage = [&](int32_t op, int32_t price, int32_t q) {
+                        const int32_t oid = (int32_t)((1u << 30) + (uint32_t)es.id_counter);
+                        es.id_counter += 1;
+                        es.submitted += q;
                         if (l == 0) {
-                            c_kind[4] += 1;
-                            q_market += q;
+                            agent_buf[2 * count] = make_int4(op, -1, price, q);
+                            agent_buf[2 * count + 1] = make_int4(oid, a.agent_tid, tlo, thi);
+                            if (op == OP_MARKET_ASK) {
+                                c_kind[4] += 1;
+                                q_market += q;
+                            } else {
+                                c_kind[2] += 1;
+                                q_limit += q;
+                            }
                         }
-                        apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, OP_MARKET_ASK, 0, q, oid,
-                                         a.agent_tid, tlo, thi, ts, tally, obs);
+                        count += 1;
+                    };
+                    // initial mid of the episode (after the first data window)
+                    if (t == 0) {
+                        const int32_t bb = n_bid > 0 ? bk.template best_px<0>() : 0;
+                        const int32_t ba = n_ask > 0 ? bk.template best_px<1>() : 0;
+                        if (n_bid > 0 && n_ask > 0)
+                            es.p_init = __ddiv_rn(__dadd_rn((double)bb, (double)ba), 2.0);
+                        else if (n_bid > 0)
+                            es.p_init = (double)bb;
+                        else if (n_ask > 0)
+                            es.p_init = (double)ba;
+                        else
+                            es.p_init = (double)a.p_fallback;
+                    }
+                    if (t < a.n_steps - 1) {
+                        if (n_ask > 0) es.last_ask = bk.template best_px<1>();
+                        const int64_t remaining = (int64_t)a.parent - es.submitted;
+                        const int64_t steps_left = (int64_t)a.n_steps - t;
+                        const int64_t target =
+                            remaining > 0 ? (remaining + steps_left - 1) / steps_left : 0;
+                        const uint32_t w = a.draws[(int64_t)r * a.n_envs + b];
+                        const int nchild = (int)(w & 3u) + 1;
+                        const int64_t base_q = target / nchild, extra = target % nchild;
+                        for (int k = 0; k < nchild; ++k) {
+                            const int32_t q = (int32_t)(base_q + (k == 0 ? extra : 0));
+                            if (q <= 0) continue;
+                            const int32_t act = (int32_t)((w >> (2 + 3 * k)) & 7u);
+                            if (act == 5)
+                                stage(OP_MARKET_ASK, 0, q);
+                            else
+                                stage(OP_LIMIT_ASK, max(1, es.last_ask + act - 2), q);
+                        }
                     } else {
-                        if (l == 0) {
-                            c_kind[2] += 1;
-                            q_limit += q;
-                        }
-                        const int32_t price = max(1, es.last_ask + act - 2);
-                        apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, OP_LIMIT_ASK, price, q,
-                                         oid, a.agent_tid, tlo, thi, ts, tally, obs);
-                    }
-                }
-            } else {
-                // last step: cancel the agent's resting orders in priority order
-                while (n_ask > 0) {
-                    SideVec<K> tmp;
-                    SideVec<K>& v = bk.template acquire<1>(tmp);
-                    int jj = -1;
+                        // last step: cancel the agent's resting orders in priority order
+                        while (n_ask > 0) {
+                            SideVec<K> tmp;
+                            SideVec<K>& v = bk.template acquire<1>(tmp);
+                            int jj = -1;
 #pragma unroll
-                    for (int j = K - 1; j >= 0; --j)
-                        if (l * K + j < n_ask && v.tid[j] == a.agent_tid) jj = j;
-                    const unsigned hit = __ballot_sync(kFull, jj >= 0);
-                    if (hit == 0) break;
-                    const int L = __ffs(hit) - 1;
-                    const int j_hit = __shfl_sync(kFull, jj, L);
-                    const int p = L * K + j_hit;
-                    const int32_t q = __shfl_sync(kFull, pick<K>(v.q, j_hit), L);
-                    shift_out<K>(v.px, p, n_ask);
-                    shift_out<K>(v.q, p, n_ask);
-                    shift_out<K>(v.oid, p, n_ask);
-                    shift_out<K>(v.tid, p, n_ask);
-                    shift_out<K>(v.tlo, p, n_ask);
-                    shift_out<K>(v.thi, p, n_ask);
-                    bk.template release<1>(v, lane_touches<K>(p, n_ask - 1));
-                    if constexpr (!Book::kInRegisters) __syncwarp();
-                    n_ask -= 1;
-                    tally.cancel_hit += 1;
-                    tally.cancelled_qty += q;
-                    if (l == 0) c_kind[3] += 1;
-                    n_msgs += 1;
-                }
-                // ... then sell what is left at market
-                const int64_t left = (int64_t)a.parent - (es.executed + warp_sum64(obs.aq));
-                if (left > 0) {
-                    const int32_t oid = (int32_t)((1u << 30) + (uint32_t)es.id_counter);
-                    es.id_counter += 1;
-                    es.submitted += left;
-                    n_msgs += 1;
-                    if (l == 0) {
-                        c_kind[4] += 1;
-                        q_market += left;
+                            for (int j = K - 1; j >= 0; --j)
+                                if (l * K + j < n_ask && v.tid[j] == a.agent_tid) jj = j;
+                            const unsigned hit = __ballot_sync(kFull, jj >= 0);
+                            if (hit == 0) break;
+                            const int L = __ffs(hit) - 1;
+                            const int j_hit = __shfl_sync(kFull, jj, L);
+                            const int p = L * K + j_hit;
+                            const int32_t q = __shfl_sync(kFull, pick<K>(v.q, j_hit), L);
+                            shift_out<K>(v.px, p, n_ask);
+                            shift_out<K>(v.q, p, n_ask);
+                            shift_out<K>(v.oid, p, n_ask);
+                            shift_out<K>(v.tid, p, n_ask);
+                            shift_out<K>(v.tlo, p, n_ask);
+                            shift_out<K>(v.thi, p, n_ask);
+                            bk.template release<1>(v, lane_touches<K>(p, n_ask - 1));
+                            if constexpr (!Book::kInRegisters) __syncwarp();
+                            n_ask -= 1;
+                            tally.cancel_hit += 1;
+                            tally.cancelled_qty += q;
+                            if (l == 0) c_kind[3] += 1;
+                            n_msgs += 1;
+                        }
+                        // ... then sell what is left at market
+                        const int64_t left =
+                            (int64_t)a.parent - (es.executed + warp_sum64(obs.aq));
+                        if (left > 0) stage(OP_MARKET_ASK, 0, (int32_t)left);
                     }
-                    apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, OP_MARKET_ASK, 0,
-                                     (int32_t)left, oid, a.agent_tid, tlo, thi, ts, tally, obs);
+                    n_msgs += count;
+                    __syncwarp();
+                }
+                int4 na = src[0], nb = src[1];
+                for (int i = 0; i < count; ++i) {
+                    const int4 ha = na, hb = nb;
+                    if (i + 1 < count) {
+                        na = src[2 * i + 2];
+                        nb = src[2 * i + 3];
+                    }
+                    apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
+                                     hb.y, hb.z, hb.w, ts, tally, obs);
                 }
             }
             n_trades += ts.count;
