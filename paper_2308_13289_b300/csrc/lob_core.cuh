@@ -747,37 +747,69 @@ __device__ __forceinline__ int32_t classify(int32_t T, int32_t S, int32_t P, int
 }
 
 // Apply one classified message to the book (Sec. 4.2 dispatch; n_bid / n_ask
-// are the warp-uniform side counts).  Every branch is warp-uniform.
-template <int K, class Book, class Obs>
+// are the warp-uniform side counts).  Every branch is warp-uniform.  The full
+// form takes one branch per case (fewest branches on the common path); the
+// compact form shares the matching code of limit and market orders (half the
+// inlined code, for kernels whose instruction cache is the constraint).
+template <int K, bool kCompact, class Book, class Obs>
 __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, int cap, int rule,
                                               int32_t op, int32_t P, int32_t Q, int32_t oid,
                                               int32_t tid, int32_t tlo, int32_t thi, TradeSink& ts,
                                               Tally& ctr, Obs& obs)
 {
-    if (op == OP_CANCEL_BID || op == OP_CANCEL_ASK) {  // cancel and delete: identical
-        if (op == OP_CANCEL_BID)
-            cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
-        else
-            cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
-    } else if (op != OP_SKIP) {
-        // limit: match, then rest the remainder; market: match at price max_int
-        // (buy) / 0 (sell), then drop the remainder
-        const bool market = op >= OP_MARKET_BID;
-        int32_t rest = Q;
-        if (op == OP_LIMIT_BID || op == OP_MARKET_BID) {
-            const int32_t Pm = market ? kMaxInt : P;
-            if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), Pm))
-                rest = match_order<K, 1>(bk, n_ask, Pm, rest, oid, tid, tlo, thi, ts, ctr, obs);
-            if (!market && rest > 0)
-                add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
-        } else {
-            const int32_t Pm = market ? 0 : P;
-            if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), Pm))
-                rest = match_order<K, 0>(bk, n_bid, Pm, rest, oid, tid, tlo, thi, ts, ctr, obs);
-            if (!market && rest > 0)
-                add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+    if constexpr (!kCompact) {
+        if (op <= OP_LIMIT_ASK) {
+            if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
+                int32_t rest = Q;
+                if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), P))
+                    rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+            } else if (op == OP_LIMIT_ASK) {
+                int32_t rest = Q;
+                if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), P))
+                    rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+            }
+        } else if (op <= OP_CANCEL_ASK) {  // cancel and delete are treated identically
+            if (op == OP_CANCEL_BID)
+                cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
+            else
+                cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
+        } else {  // market: price max_int (buy) / 0 (sell), remainder dropped
+            int32_t rest = Q;
+            if (op == OP_MARKET_BID) {
+                if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr, obs);
+            } else {
+                if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr, obs);
+            }
+            ctr.discarded_qty += rest;
         }
-        if (market) ctr.discarded_qty += rest;
+    } else {
+        if (op == OP_CANCEL_BID || op == OP_CANCEL_ASK) {  // cancel and delete: identical
+            if (op == OP_CANCEL_BID)
+                cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
+            else
+                cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
+        } else if (op != OP_SKIP) {
+            // limit: match, then rest the remainder; market: match at price max_int
+            // (buy) / 0 (sell), then drop the remainder
+            const bool market = op >= OP_MARKET_BID;
+            int32_t rest = Q;
+            if (op == OP_LIMIT_BID || op == OP_MARKET_BID) {
+                const int32_t Pm = market ? kMaxInt : P;
+                if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), Pm))
+                    rest = match_order<K, 1>(bk, n_ask, Pm, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                if (!market && rest > 0)
+                    add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+            } else {
+                const int32_t Pm = market ? 0 : P;
+                if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), Pm))
+                    rest = match_order<K, 0>(bk, n_bid, Pm, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                if (!market && rest > 0)
+                    add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
+            }
+            if (market) ctr.discarded_qty += rest;
+        }
     }
     if constexpr (!Book::kInRegisters) __syncwarp();
 }

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                     na = mb[2 * i + 2];
                     nb = mb[2 * i + 3];
                 }
-                apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
+                apply_message<K, false>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
                                  hb.z, hb.w, ts, tally, obs);
             }
             __syncwarp();

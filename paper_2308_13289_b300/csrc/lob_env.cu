@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                         na = src[2 * i + 2];
                         nb = src[2 * i + 3];
                     }
-                    apply_message<K>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
+                    apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
                                      hb.y, hb.z, hb.w, ts, tally, obs);
                 }
             }
