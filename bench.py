@@ -183,8 +183,23 @@ def run_engine(args):
 
     # ---------------- persistent form
     e = eng.Engine(n, cap, tcap)
+    launch = None
     if args.launch:
         e.set_launch(*[int(x) for x in args.launch.split(",")])
+        launch = {"override": args.launch}
+    elif counts.min() == counts.max() and counts[0] >= 5000:
+        # autotune warps/CTA and chunk on the first 5,000 messages of every book
+        from paper_2308_13289_b300 import autotune
+        per = int(counts[0])
+        pre = d_msgs.view(n, per, 8)[:, :5000].contiguous().view(-1, 8)
+        pre_off = torch.arange(0, n * 5000 + 1, 5000, dtype=torch.int64, device="cuda")
+        shape = autotune.tune(n, cap, pre, pre_off, trade_capacity=5000, mean_msgs=per)
+        autotune.apply(e, shape)
+        launch = {"warps_per_cta": shape["warps"], "chunk_msgs": shape["chunk"],
+                  "autotuned_on": "first 5,000 messages of every book", "cached": shape["cached"],
+                  "table_ms": {"%d,%d" % (t["warps"], t["chunk"]): round(t["ms"], 3)
+                               for t in shape["table"]}}
+        del pre, pre_off
     lv_out = [torch.empty((n, depth), dtype=torch.int32, device="cuda") for _ in range(4)]
 
     def step_persistent(ev=None):
@@ -340,7 +355,7 @@ def run_engine(args):
                 "config": {"workload": args.workload, "n_books_per_gpu": n,
                            "capacity": cap, "messages_per_step_per_gpu": total_msgs,
                            "trades_per_step_per_gpu": trades_per_step,
-                           "trade_capacity": tcap, "form": "persistent",
+                           "trade_capacity": tcap, "form": "persistent", "launch": launch,
                            "l2": "inputs larger than L2 (%.2f GB of messages)" % (total_msgs * 32 / 1e9),
                            "seed": w["seed"]},
                 "plain": plain, "plain_graph": plain_graph,
