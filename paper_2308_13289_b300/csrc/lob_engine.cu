@@ -12,6 +12,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -44,6 +45,24 @@ int lob_cuda_fail(cudaError_t e, const char* where)
 {
     lob_set_error("%s: %s", where, cudaGetErrorString(e));
     return LOB_E_CUDA;
+}
+
+// The dynamic shared-memory limit is an attribute of the kernel function, shared
+// by every context in the process: only ever raise it, so that configuring one
+// context never invalidates the launch shape of another.
+cudaError_t lob_raise_smem_limit(const void* fn, int bytes)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, int> current;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int& cur = current[std::make_pair(dev, fn)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -478,7 +497,7 @@ static int configure_launch(lob_ctx* c, int W, int chunk, int ctas_per_sm)
         return LOB_E_INVAL;
     }
     const void* fn = process_kernel(c->K);
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    e = lob_raise_smem_limit(fn, smem);
     if (e != cudaSuccess) return lob_cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * W, smem);
@@ -871,7 +890,7 @@ int static_setup(int dev, StaticSetup** out)
             const int K = ks[i], W = static_warps(K);
             const int smem = smem_per_warp(K, kStaticChunk) * W;
             const void* fn = process_kernel(K);
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = lob_raise_smem_limit(fn, smem);
             if (e != cudaSuccess) return lob_cuda_fail(e, "cudaFuncSetAttribute");
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s.per_sm[i], fn, 32 * W, smem);
             if (e != cudaSuccess) return lob_cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");

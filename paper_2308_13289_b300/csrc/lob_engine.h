@@ -30,6 +30,7 @@ struct lob_ctx {
 void lob_set_error(const char* fmt, ...);
 int lob_cuda_fail(cudaError_t e, const char* where);
 int lob_book_bytes(int K);
+cudaError_t lob_raise_smem_limit(const void* fn, int bytes);
 int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
                        const int32_t* d_book_ids, int32_t n_active, int append,
                        cudaStream_t stream, const int64_t* d_counts);

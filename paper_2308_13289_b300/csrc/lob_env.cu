@@ -450,8 +450,7 @@ int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, vo
         return LOB_E_INVAL;
     }
     if (err == cudaSuccess)
-        err = cudaFuncSetAttribute(env_kernel(K), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   e->smem_per_cta);
+        err = lob_raise_smem_limit(env_kernel(K), e->smem_per_cta);
     if (err == cudaSuccess)
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->per_sm, env_kernel(K),
                                                             32 * e->warps, e->smem_per_cta);

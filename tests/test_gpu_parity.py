@@ -201,3 +201,16 @@ def test_argument_errors(eng):
         eng.Engine(1, 513, 8)
     with pytest.raises(eng.LobError):
         eng.Engine(0, 100, 8)
+
+
+def test_contexts_with_different_launch_shapes_coexist(eng):
+    """Configuring one context (smaller shape) never invalidates another's."""
+    msgs, off = lobgen.generate(lobgen.make_params(8), [3000] * 16)
+    d, o = eng.messages_to_device(msgs), torch.from_numpy(off).cuda()
+    big = eng.Engine(16, 100, 4096)
+    big.set_launch(8, 256, 0)
+    small = eng.Engine(16, 100, 4096)
+    small.set_launch(1, 8, 0)
+    big.process_batch(d, o)
+    small.process_batch(d, o)
+    assert_same(gpu_outputs(big), gpu_outputs(small))
