@@ -64,10 +64,8 @@ def parse():
 # ------------------------------------------------------------------ helpers
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2308_13289_b300 import dist as ldist
+    return ldist.rank_world()
 
 
 class ClockSampler:
@@ -140,7 +138,8 @@ def workload_streams(name, rank):
     else:
         counts = lobgen.lognormal_counts(n, w["seed"])
     params = lobgen.make_params(w["seed"], w["mid_walk"])
-    sid = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
+    from paper_2308_13289_b300 import dist as ldist
+    sid = ldist.stream_ids(rank, n)
     msgs, off = lobgen.generate(params, counts, stream_ids=sid)
     return w, params, counts, msgs, off, sid
 
@@ -561,13 +560,8 @@ def eng_book_bytes(cap):
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2308_13289_b300 import dist as ldist
+    return x if world == 1 else ldist.max_over_ranks(x, device="cuda")
 
 
 def time_steps(fn, args, stream, barrier, world, steps=None):

@@ -1,0 +1,116 @@
+"""Parity at the full workload sizes in the launch configuration bench.py
+times (autotuned persistent launch), on sampled outputs the oracle computes
+book by book from the books' own streams."""
+import numpy as np
+import pytest
+import torch
+
+import lobgen
+import oracle
+from engine_harness import oracle_outputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import paper_2308_13289_b300 as eng
+    from paper_2308_13289_b300 import build
+    build.build()
+    return eng
+
+
+def _sampled(g, books, o):
+    ref = oracle_outputs(o)
+    for k in ("book_price", "book_qty", "book_oid", "book_tid", "book_time_ns", "book_count",
+              "trade_counts", "bid_px", "bid_qty", "ask_px", "ask_qty", "counters"):
+        assert np.array_equal(g[k][books], ref[k]), k
+    n_tr = min(4, len(books))
+    assert np.array_equal(g["trades"][books[:n_tr]], ref["trades"][:n_tr])
+
+
+def test_replay_1024x100k_full_size(eng, tmp_path, monkeypatch):
+    from engine_harness import gpu_outputs
+    from paper_2308_13289_b300 import autotune
+    monkeypatch.setenv(autotune.CACHE_ENV, str(tmp_path / "tune.json"))
+    w = lobgen.WORKLOADS["replay_1024x100k"]
+    n, per = w["n_books"], w["msgs"]
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    dm, doff = lobgen.DeviceStreams(params, n).advance([per] * n)
+    tcap = int(per * 0.75) + 1024
+    e = eng.Engine(n, w["capacity"], tcap)
+    pre = dm.view(n, per, 8)[:, :5000].contiguous().view(-1, 8)
+    pre_off = torch.arange(0, n * 5000 + 1, 5000, dtype=torch.int64, device="cuda")
+    autotune.apply(e, autotune.tune(n, w["capacity"], pre, pre_off, trade_capacity=5000,
+                                    mean_msgs=per, reps=1))
+    e.process_batch(dm, doff)
+    g = gpu_outputs(e)
+    assert g["status"] == 0
+    books = np.array([0, 1, 2, 100, 511, 512, 900, 1022, 1023])
+    hm, hoff = lobgen.generate(params, [per] * len(books), stream_ids=books.astype(np.uint64))
+    o = oracle.Oracle(len(books), w["capacity"], tcap)
+    o.process(hm, hoff)
+    _sampled(g, books, o)
+    # the plain form: one launch per 100-message chunk, trades appended
+    chunk = w["chunk"]
+    nch = per // chunk
+    cm = torch.empty_like(dm)
+    cm.view(nch, n, chunk, 8).copy_(dm.view(n, nch, chunk, 8).transpose(0, 1))
+    del pre
+    ep = eng.Engine(n, w["capacity"], tcap, append_trades=True)
+    seg = torch.arange(0, n * chunk + 1, chunk, dtype=torch.int64, device="cuda")
+    for c in range(nch):
+        ep.process_batch(cm[c * n * chunk:(c + 1) * n * chunk], seg)
+    gp = gpu_outputs(ep)
+    for k in g:
+        if k != "status":
+            assert np.array_equal(gp[k], g[k]), k
+
+
+def test_uneven_4096_full_size_longest_first(eng):
+    from engine_harness import gpu_outputs
+    w = lobgen.WORKLOADS["uneven_4096_lognormal"]
+    n = w["n_books"]
+    counts = lobgen.lognormal_counts(n, w["seed"])
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    perm = np.argsort(-counts, kind="stable")
+    dm, doff = lobgen.DeviceStreams(params, n).advance(counts[perm], ids=perm.astype(np.int32))
+    tcap = int(counts.max() * 0.75) + 1024
+    e = eng.Engine(n, w["capacity"], tcap)
+    e.process_batch(dm, doff, torch.from_numpy(perm.astype(np.int32)).cuda())
+    g = gpu_outputs(e)
+    assert g["status"] == 0
+    books = np.array(sorted({0, 1, int(perm[0]), int(perm[1]), int(perm[-1]), 2047, 4095}))
+    hm, hoff = lobgen.generate(params, counts[books], stream_ids=books.astype(np.uint64))
+    o = oracle.Oracle(len(books), w["capacity"], tcap)
+    o.process(hm, hoff)
+    _sampled(g, books, o)
+
+
+def test_rl_exec_8192x400_full_size(eng):
+    w = lobgen.WORKLOADS["rl_exec_8192x400"]
+    n, steps, per = w["n_books"], w["steps"], w["msgs_per_step"]
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    dm, _ = lobgen.DeviceStreams(params, n).advance([steps * per] * n)
+    draws = lobgen.agent_draws_device(w["seed"] + 1, n, steps)
+    e = eng.Engine(n, w["capacity"], 4096)
+    env = eng.Env(e, n_steps=steps, msgs_per_step=per)
+    out = env.run(dm, steps * per, 0, steps, draws)
+    torch.cuda.synchronize()
+    sample = np.array([0, 4097, n - 1])
+    hm, _ = lobgen.generate(params, [steps * per] * len(sample), stream_ids=sample.astype(np.uint64))
+    hd = lobgen.agent_draws(w["seed"] + 1, n, steps)[:, sample]
+    oenv = oracle.EnvOracle(len(sample), w["capacity"], 4096, n_steps=steps)
+    rows = hm.reshape(len(sample), steps, per)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    for t in range(steps):
+        stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
+        r_, lv, f_ = oenv.step(stp, np.arange(0, len(sample) * per + 1, per), hd[t], t)
+        assert g["reward"][t, sample].tobytes() == r_.tobytes(), t
+        assert np.array_equal(g["fills"][t, sample], f_), t
+        for name, v in zip(("bid_px", "bid_qty", "ask_px", "ask_qty"), lv):
+            assert np.array_equal(g[name][t, sample], v), (name, t)
+    st, p0 = env.state()
+    ost, op0 = oenv.state()
+    assert np.array_equal(st.cpu().numpy()[sample], ost)
+    assert p0.cpu().numpy()[sample].tobytes() == op0.tobytes()
