@@ -475,10 +475,10 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<X>(tmp);
     // insertion point: number of resting orders with a price at least as good
-    unsigned cnt = 0;
+    int p = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) cnt += (l * K + j < n && at_least<X>(v.px[j], P)) ? 1u : 0u;
-    const int p = (int)__reduce_add_sync(kFull, cnt);
+    for (int j = 0; j < K; ++j)
+        p += __popc(__ballot_sync(kFull, l * K + j < n && at_least<X>(v.px[j], P)));
     const bool full = n >= cap;
     if (full && (rule != 0 || p >= cap)) {
         ctr.rejected += 1;
