@@ -92,6 +92,8 @@ def _oracle_lib():
     lib.oracle_destroy.argtypes = [vp]
     lib.oracle_process.restype = ctypes.c_int64
     lib.oracle_process.argtypes = [vp, vp, vp, vp, i32, i32]
+    lib.oracle_process_l1.restype = ctypes.c_int64
+    lib.oracle_process_l1.argtypes = [vp, vp, vp, vp, i32, i32, vp]
     lib.oracle_clear_trades.argtypes = [vp]
     lib.oracle_get_trades.argtypes = [vp, vp, vp]
     lib.oracle_get_book.argtypes = [vp, vp, vp, vp, vp, vp, vp]
@@ -140,6 +142,21 @@ class Oracle:
                                       _p(ids), n_active, threads or default_threads())
         if err:
             raise RuntimeError("oracle: %d duplicate live OIDs (contract violation)" % err)
+
+    def process_l1(self, msgs: np.ndarray, offsets: np.ndarray, book_ids=None, threads=None):
+        """process() and return the level-1 state after every message:
+        int32 [len(msgs), 4] = bid price, bid qty, ask price, ask qty."""
+        msgs = np.ascontiguousarray(msgs, dtype=MSG_DTYPE)
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        ids = None if book_ids is None else np.ascontiguousarray(book_ids, dtype=np.int32)
+        n_active = len(offsets) - 1
+        l1 = np.full((len(msgs), 4), -7, np.int32)
+        err = self.lib.oracle_process_l1(self.h, _p(msgs) if len(msgs) else None, _p(offsets),
+                                         _p(ids), n_active, threads or default_threads(),
+                                         _p(l1) if len(msgs) else None)
+        if err:
+            raise RuntimeError("oracle: %d duplicate live OIDs (contract violation)" % err)
+        return l1
 
     def clear_trades(self):
         self.lib.oracle_clear_trades(self.h)

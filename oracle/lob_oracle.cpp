@@ -323,6 +323,26 @@ static void process(Engine& E, Book& bk, const Msg& m)
     }
 }
 
+// Level-1 state of a book (Sec. 5.2.1): best bid price and the quantity at
+// that price, best ask price and the quantity at that price; an empty side is
+// (-1, 0); quantities saturate at max_int.
+static void level1(Book& bk, int32_t* out4)
+{
+    Side* sides[2] = {&bk.bids, &bk.asks};
+    for (int s = 0; s < 2; ++s) {
+        Side& sd = *sides[s];
+        if (sd.empty()) {
+            out4[2 * s] = -1;
+            out4[2 * s + 1] = 0;
+            continue;
+        }
+        int64_t vol = 0;
+        for (const auto& o : sd.best_level()) vol += o.qty;
+        out4[2 * s] = sd.best().price;
+        out4[2 * s + 1] = (int32_t)std::min<int64_t>(vol, MAX_INT);
+    }
+}
+
 template <class F>
 static void parallel_for(int32_t n, int32_t n_threads, F&& body)
 {
@@ -383,6 +403,33 @@ int64_t oracle_process(void* h, const Msg* msgs, const int64_t* offsets, const i
         }
         int32_t e0 = bk.error;
         for (int64_t k = offsets[i]; k < offsets[i + 1]; ++k) process(E, bk, msgs[k]);
+        err[(size_t)i] = bk.error - e0;
+    });
+    int64_t total = 0;
+    for (int32_t e : err) total += e;
+    return total;
+}
+
+// As oracle_process, and writes the level-1 state after every message:
+// l1[k][4] = {bid price, bid qty, ask price, ask qty} for message k of `msgs`.
+int64_t oracle_process_l1(void* h, const Msg* msgs, const int64_t* offsets,
+                          const int32_t* book_ids, int32_t n_active, int32_t n_threads,
+                          int32_t* l1)
+{
+    Engine& E = *(Engine*)h;
+    std::vector<int32_t> err((size_t)std::max(n_active, 0), 0);
+    parallel_for(n_active, n_threads, [&](int32_t i) {
+        int32_t b = book_ids ? book_ids[i] : i;
+        Book& bk = E.books[(size_t)b];
+        if (!E.append_trades) {
+            bk.log.clear();
+            bk.log_count = 0;
+        }
+        int32_t e0 = bk.error;
+        for (int64_t k = offsets[i]; k < offsets[i + 1]; ++k) {
+            process(E, bk, msgs[k]);
+            level1(bk, l1 + 4 * k);
+        }
         err[(size_t)i] = bk.error - e0;
     });
     int64_t total = 0;

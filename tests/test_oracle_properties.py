@@ -195,3 +195,32 @@ def test_set_book_roundtrip():
     o2.set_book(bk)
     for k, v in o2.book().items():
         assert np.array_equal(v, bk[k])
+
+
+def test_level1_trace_matches_levels_after_each_message():
+    """The level-1 trace after message k equals level 0 of the top-level
+    output computed on the book as it stands after message k."""
+    p = lobgen.make_params(61, "pm1")
+    msgs, _ = lobgen.generate(p, [600])
+    o1 = oracle.Oracle(1, 20, 256)
+    l1 = o1.process_l1(msgs, np.array([0, len(msgs)], np.int64))
+    o2 = oracle.Oracle(1, 20, 256)
+    one = np.array([0, 1], np.int64)
+    for k in range(len(msgs)):
+        o2.process(msgs[k:k + 1], one)
+        bp, bq, ap, aq = o2.levels(1)
+        assert tuple(l1[k]) == (bp[0, 0], bq[0, 0], ap[0, 0], aq[0, 0]), k
+
+
+def test_level1_trace_hand_example():
+    # levels_aggregate.lob: after its 7 messages level 1 is bid 100x5, ask 101x5
+    from golden_format import cases
+    c = [c for c in cases() if c.name == "levels_aggregate.lob"][0]
+    m = c.message_array()
+    o = oracle.Oracle(1, c.capacity, 16)
+    l1 = o.process_l1(m, np.array([0, len(m)], np.int64))
+    assert tuple(l1[0]) == (100, 2, -1, 0)      # first bid only
+    assert tuple(l1[2]) == (100, 5, -1, 0)      # second order at 100 joins the level
+    assert tuple(l1[4]) == (100, 5, 103, 1)
+    assert tuple(l1[5]) == (100, 5, 101, 5)
+    assert tuple(l1[6]) == (100, 5, 101, 5)
