@@ -173,6 +173,16 @@ int lob_reset_books(lob_ctx* ctx, const int32_t* d_book_ids, int32_t n, void* st
 int lob_process_batch(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_offsets,
                       const int32_t* d_book_ids, int32_t n_active, void* stream);
 
+/* lob_process_batch that also records the level-1 state after every message
+ * (the execution environment's per-message best bid/ask price and volume,
+ * Sec. 5.2.1): d_l1 is int32[total messages][4] indexed like d_msgs, entry k =
+ * {best bid price, quantity at it, best ask price, quantity at it} after
+ * message k; an empty side is (-1, 0); quantities saturate at INT32_MAX.
+ * Entries of messages outside every segment are not written. */
+int lob_process_batch_l1(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                         const int32_t* d_book_ids, int32_t n_active, int32_t* d_l1,
+                         void* stream);
+
 /* Same as lob_process_batch, but segment i is d_msgs[d_starts[i] ..
  * d_starts[i] + d_counts[i]) (int64 each, device), so the segments may lie
  * anywhere in d_msgs -- e.g. the current step window of each of many resident

@@ -93,6 +93,12 @@ def lob_process_batch(h, msgs, offsets, book_ids=None, n_active=None, stream=Non
                                   _stream(stream)), "lob_process_batch")
 
 
+def lob_process_batch_l1(h, msgs, offsets, l1, book_ids=None, n_active=None, stream=None):
+    n = (offsets.numel() - 1) if n_active is None else n_active
+    check(lib().lob_process_batch_l1(h, _ptr(msgs), _ptr(offsets), _ptr(book_ids), n, _ptr(l1),
+                                     _stream(stream)), "lob_process_batch_l1")
+
+
 def lob_process_segments(h, msgs, starts, counts, book_ids, stream=None):
     check(lib().lob_process_segments(h, _ptr(msgs), _ptr(starts), _ptr(counts), _ptr(book_ids),
                                      book_ids.numel(), _stream(stream)), "lob_process_segments")

@@ -31,6 +31,7 @@ SIGNATURES = {
     "lob_process_batch": (ctypes.c_int, [vp, vp, vp, vp, i32, vp]),
     "lob_inject_orders": (ctypes.c_int, [vp, vp, vp, vp, i32, vp]),
     "lob_process_segments": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, vp]),
+    "lob_process_batch_l1": (ctypes.c_int, [vp, vp, vp, vp, i32, vp, vp]),
     "lob_clear_trades": (ctypes.c_int, [vp, vp]),
     "lob_get_levels": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp]),
     "lob_get_trades": (ctypes.c_int, [vp, vp, vp, vp]),

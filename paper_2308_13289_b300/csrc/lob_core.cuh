@@ -859,4 +859,24 @@ __device__ __forceinline__ void emit_levels(const int32_t (&px)[K], const int32_
     __syncwarp();
 }
 
+// Level-1 state of one side after a message (Sec. 5.2.1): best price and the
+// summed quantity of the orders at it (the level-0 prefix of the sorted side),
+// (-1, 0) when empty, quantity saturating at INT32_MAX.
+template <int K, int X, class Book>
+__device__ __forceinline__ int2 level1_side(Book& bk, int n)
+{
+    if (n == 0) return make_int2(-1, 0);
+    const int l = lane_id();
+    SideVec<K> tmp;
+    SideVec<K>& v = bk.template acquire<X>(tmp);
+    const int32_t best = __shfl_sync(kFull, v.px[0], 0);
+    int64_t loc = 0;
+#pragma unroll
+    for (int j = 0; j < K; ++j) loc += (l * K + j < n && v.px[j] == best) ? v.q[j] : 0;
+    // the level ends inside lane 0 unless lane 0's last slot is still at the best price
+    const bool spans = __shfl_sync(kFull, (int)(K < n && v.px[K - 1] == best), 0) != 0;
+    const int64_t vol = spans ? warp_sum64(loc) : __shfl_sync(kFull, loc, 0);
+    return make_int2(best, (int32_t)min(vol, (int64_t)kMaxInt));
+}
+
 }  // namespace lob

@@ -87,6 +87,7 @@ struct ProcArgs {
     int32_t* queue;
     int32_t cap, rule, trade_cap, append, chunk, pad_;
     uint64_t wait_ns;
+    int32_t* l1;  // level-1 trace [message][4], or null
 };
 
 template <int K>
@@ -99,7 +100,7 @@ __host__ __device__ constexpr int warp_smem_bytes(int chunk)
 template <int K>
 constexpr int max_threads() { return K >= 4 ? 256 : 512; }
 
-template <int K>
+template <int K, bool kTrace>
 __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
 {
     using Book = typename BookPolicy<K>::type;
@@ -212,6 +213,13 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                 }
                 apply_message<K, false>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
                                  hb.z, hb.w, ts, tally, obs);
+                if constexpr (kTrace) {
+                    const int2 lb = level1_side<K, 0>(bk, n_bid);
+                    const int2 la = level1_side<K, 1>(bk, n_ask);
+                    if (l == 0)
+                        reinterpret_cast<int4*>(a.l1)[lo + (int64_t)c * chunk + i] =
+                            make_int4(lb.x, lb.y, la.x, la.y);
+                }
             }
             __syncwarp();
             if (c + 2 < nchunks && l == 0) {
@@ -412,14 +420,23 @@ int k_of(int capacity)
     return 16;
 }
 
-const void* process_kernel(int K)
+const void* process_kernel(int K, bool trace = false)
 {
+    if (trace) {
+        switch (K) {
+        case 1: return reinterpret_cast<const void*>(&k_process<1, true>);
+        case 2: return reinterpret_cast<const void*>(&k_process<2, true>);
+        case 4: return reinterpret_cast<const void*>(&k_process<4, true>);
+        case 8: return reinterpret_cast<const void*>(&k_process<8, true>);
+        default: return reinterpret_cast<const void*>(&k_process<16, true>);
+        }
+    }
     switch (K) {
-    case 1: return reinterpret_cast<const void*>(&k_process<1>);
-    case 2: return reinterpret_cast<const void*>(&k_process<2>);
-    case 4: return reinterpret_cast<const void*>(&k_process<4>);
-    case 8: return reinterpret_cast<const void*>(&k_process<8>);
-    default: return reinterpret_cast<const void*>(&k_process<16>);
+    case 1: return reinterpret_cast<const void*>(&k_process<1, false>);
+    case 2: return reinterpret_cast<const void*>(&k_process<2, false>);
+    case 4: return reinterpret_cast<const void*>(&k_process<4, false>);
+    case 8: return reinterpret_cast<const void*>(&k_process<8, false>);
+    default: return reinterpret_cast<const void*>(&k_process<16, false>);
     }
 }
 
@@ -444,7 +461,7 @@ int lob_book_bytes(int K) { return 48 * 32 * K; }
 
 int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
                        const int32_t* d_book_ids, int32_t n_active, int append,
-                       cudaStream_t stream, const int64_t* d_counts)
+                       cudaStream_t stream, const int64_t* d_counts, int32_t* d_l1)
 {
     if (n_active == 0) return LOB_OK;
     ProcArgs a;
@@ -468,13 +485,19 @@ int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_off
     a.chunk = c->chunk;
     a.pad_ = 0;
     a.wait_ns = kWaitNs;
+    a.l1 = d_l1;
     const int W = c->warps_per_cta;
     int grid = (n_active + W - 1) / W;
     const int resident = c->num_sms * c->ctas_per_sm_eff;
     if (grid > resident) grid = resident;
     if (grid < 1) grid = 1;
     void* args[] = {&a};
-    cudaError_t e = cudaLaunchKernel(process_kernel(c->K), dim3(grid), dim3(32 * W), args,
+    const void* fn = process_kernel(c->K, d_l1 != nullptr);
+    if (d_l1) {
+        cudaError_t ea = lob_raise_smem_limit(fn, c->smem_per_cta);
+        if (ea != cudaSuccess) return lob_cuda_fail(ea, "cudaFuncSetAttribute");
+    }
+    cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(32 * W), args,
                                      (size_t)c->smem_per_cta, stream);
     if (e != cudaSuccess) return lob_cuda_fail(e, "lob_process_batch launch");
     c->launches += 1;
@@ -680,7 +703,22 @@ int lob_process_batch(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offs
     if (rc != LOB_OK) return rc;
     const int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
     return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, append,
-                              (cudaStream_t)stream, nullptr);
+                              (cudaStream_t)stream, nullptr, nullptr);
+}
+
+int lob_process_batch_l1(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
+                         const int32_t* d_book_ids, int32_t n_active, int32_t* d_l1,
+                         void* stream)
+{
+    int rc = check_batch(c, d_msgs, d_offsets, d_book_ids, n_active, "lob_process_batch_l1");
+    if (rc != LOB_OK) return rc;
+    if (n_active > 0 && (!d_l1 || ((uintptr_t)d_l1 & 15u) != 0)) {
+        lob_set_error("lob_process_batch_l1: the trace must be a 16-byte aligned buffer");
+        return LOB_E_INVAL;
+    }
+    const int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
+    return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, append,
+                              (cudaStream_t)stream, nullptr, d_l1);
 }
 
 int lob_process_segments(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_starts,
@@ -695,7 +733,7 @@ int lob_process_segments(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_s
     }
     const int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
     return lob_launch_process(c, d_msgs, d_starts, d_book_ids, n_active, append,
-                              (cudaStream_t)stream, d_counts);
+                              (cudaStream_t)stream, d_counts, nullptr);
 }
 
 int lob_inject_orders(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
@@ -704,7 +742,7 @@ int lob_inject_orders(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offs
     int rc = check_batch(c, d_msgs, d_offsets, d_book_ids, n_active, "lob_inject_orders");
     if (rc != LOB_OK) return rc;
     return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, 1,
-                              (cudaStream_t)stream, nullptr);
+                              (cudaStream_t)stream, nullptr, nullptr);
 }
 
 int lob_clear_trades(lob_ctx* c, void* stream)
@@ -986,6 +1024,7 @@ extern "C" int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t
     a.chunk = kStaticChunk;
     a.pad_ = 0;
     a.wait_ns = kWaitNs;
+    a.l1 = nullptr;
     const int W = static_warps(K);
     int grid = (n_books + W - 1) / W;
     const int resident = s->num_sms * s->per_sm[k_index(K)];

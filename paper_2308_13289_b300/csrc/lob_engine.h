@@ -33,4 +33,4 @@ int lob_book_bytes(int K);
 cudaError_t lob_raise_smem_limit(const void* fn, int bytes);
 int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,
                        const int32_t* d_book_ids, int32_t n_active, int append,
-                       cudaStream_t stream, const int64_t* d_counts);
+                       cudaStream_t stream, const int64_t* d_counts, int32_t* d_l1);

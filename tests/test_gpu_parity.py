@@ -214,3 +214,17 @@ def test_contexts_with_different_launch_shapes_coexist(eng):
     big.process_batch(d, o)
     small.process_batch(d, o)
     assert_same(gpu_outputs(big), gpu_outputs(small))
+
+
+@pytest.mark.parametrize("cap", [7, 100, 250, 500])
+def test_level1_trace_matches_oracle(eng, cap):
+    counts = [2500, 0, 1, 1999, 4096, 300]
+    msgs, off = lobgen.generate(lobgen.make_params(4000 + cap), counts)
+    e = eng.Engine(len(counts), cap, 4096)
+    l1 = torch.full((len(msgs), 4), -7, dtype=torch.int32, device="cuda")
+    eng.lob_process_batch_l1(e.h, eng.messages_to_device(msgs), torch.from_numpy(off).cuda(), l1)
+    o = oracle.Oracle(len(counts), cap, 4096)
+    exp = o.process_l1(msgs, off)
+    assert np.array_equal(l1.cpu().numpy(), exp)
+    # the traced run leaves the same books and trades as an untraced one
+    assert_same(gpu_outputs(e), oracle_outputs(o))
