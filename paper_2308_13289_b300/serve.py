@@ -13,9 +13,13 @@ current windows (lob_process_segments), each class on its own CUDA stream so
 the classes overlap on the device.  Episodes that finish free their slot in
 the same tick, so later arrivals join a batch that is already running.
 
-Latency of an episode-step = wall time of the tick that ran it; the report
-gives p50/p99 over all episode-steps, steps/s and messages/s, the admission
-wait and the queue length over time.
+The host runs up to RING ticks ahead of the GPU (finishing times are known
+from the step counts, so no tick waits for the previous one); the latency of
+an episode-step is the GPU time of its pool's tick, measured by events around
+that tick's work on the pool's stream.  The report gives p50/p99 over all
+episode-steps, steps/s and messages/s, the admission wait and the queue length
+over time.  (With collect=True, used by the tests, every tick is synchronous
+and timed on the host.)
 """
 from __future__ import annotations
 
@@ -31,6 +35,7 @@ import torch
 from . import Engine, lib, lob_get_levels
 
 MSG_BYTES = 32
+RING = 8  # ticks the host may run ahead of the GPU
 
 
 @dataclasses.dataclass
@@ -83,9 +88,14 @@ class _Pool:
             self.levels = [torch.empty((slots, depth), dtype=torch.int32, device="cuda")
                            for _ in range(4)]
             self.d_tcount = torch.empty(slots, dtype=torch.int64, device="cuda")
-        self.h_ids = torch.empty(slots, dtype=torch.int32).pin_memory()
-        self.h_start = torch.empty(slots, dtype=torch.int64).pin_memory()
-        self.h_cnt = torch.empty(slots, dtype=torch.int64).pin_memory()
+            self.d_slot = torch.arange(slots, dtype=torch.int32, device="cuda")
+        # a ring of pinned staging sets, so the host can run ahead of the GPU;
+        # a set is reused only after the event recorded behind its copies
+        self.ring = [dict(ids=torch.empty(slots, dtype=torch.int32).pin_memory(),
+                          start=torch.empty(slots, dtype=torch.int64).pin_memory(),
+                          cnt=torch.empty(slots, dtype=torch.int64).pin_memory(),
+                          used=torch.cuda.Event(), busy=False) for _ in range(RING)]
+        self.ring_pos = 0
         self.free = list(range(slots - 1, -1, -1))
         self.ep = np.full(slots, -1, np.int64)      # episode index in the slot, -1 free
         self.step = np.zeros(slots, np.int64)
@@ -101,22 +111,33 @@ class _Pool:
         self.n_steps[s], self.mps[s], self.base[s] = ep.n_steps, ep.msgs_per_step, ep.base
         self.n_active += 1
         with torch.cuda.stream(self.stream):
-            self.engine.reset_books(torch.tensor([s], dtype=torch.int32, device="cuda"))
+            self.engine.reset_books(self.d_slot[s:s + 1])
 
-    def launch_step(self, d_msgs):
-        """One step of every active slot, asynchronously on this pool's stream."""
+    def launch_step(self, d_msgs, timing=False):
+        """One step of every active slot, asynchronously on this pool's stream.
+        Returns (active slots, messages, (start, end) events or None)."""
         act = np.flatnonzero(self.ep >= 0).astype(np.int32)
         n = len(act)
         cnt = self.mps[act]
-        self.h_ids.numpy()[:n] = act
-        self.h_start.numpy()[:n] = self.base[act] + self.step[act] * cnt
-        self.h_cnt.numpy()[:n] = cnt
+        st = self.ring[self.ring_pos]
+        self.ring_pos = (self.ring_pos + 1) % len(self.ring)
+        if st["busy"]:
+            st["used"].synchronize()
+        st["ids"].numpy()[:n] = act
+        st["start"].numpy()[:n] = self.base[act] + self.step[act] * cnt
+        st["cnt"].numpy()[:n] = cnt
         s = ctypes.c_void_p(self.stream.cuda_stream)
         p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        ev = None
         with torch.cuda.stream(self.stream):
-            self.d_ids[:n].copy_(self.h_ids[:n], non_blocking=True)
-            self.d_start[:n].copy_(self.h_start[:n], non_blocking=True)
-            self.d_cnt[:n].copy_(self.h_cnt[:n], non_blocking=True)
+            if timing:
+                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev[0].record(self.stream)
+            self.d_ids[:n].copy_(st["ids"][:n], non_blocking=True)
+            self.d_start[:n].copy_(st["start"][:n], non_blocking=True)
+            self.d_cnt[:n].copy_(st["cnt"][:n], non_blocking=True)
+            st["used"].record(self.stream)
+            st["busy"] = True
             rc = lib().lob_process_segments(self.engine.h, p(d_msgs), p(self.d_start),
                                             p(self.d_cnt), p(self.d_ids), n, s)
             if rc != 0:
@@ -124,7 +145,9 @@ class _Pool:
             lob_get_levels(self.engine.h, self.depth, *self.levels, stream=self.stream)
             if self.collect:
                 lib().lob_get_trades(self.engine.h, None, p(self.d_tcount), s)
-        return act, int(cnt.sum())
+            if timing:
+                ev[1].record(self.stream)
+        return act, int(cnt.sum()), ev
 
 
 class Server:
@@ -175,6 +198,7 @@ class Server:
         lat, weights, queue_len = [], [], []
         steps_done = msgs_done = 0
         max_active = max_used = 0
+        pending_ev = []
         tick = 0
         t0 = time.perf_counter()
         while pending or waiting or any(p.n_active for p in self.pools.values()):
@@ -201,19 +225,27 @@ class Server:
                     time.sleep(max(0.0, min(episodes[pending[0]].arrival - now, 0.001)))
                 tick += 1
                 continue
-            ts = time.perf_counter()
-            launched = [(p, *p.launch_step(self.d_msgs)) for p in busy]
-            for p in busy:
-                p.stream.synchronize()
-            te = time.perf_counter()
-            lat.append(te - ts)
-            weights.append(active)
+            if self.collect:
+                ts = time.perf_counter()
+                launched = [(p, *p.launch_step(self.d_msgs)) for p in busy]
+                for p in busy:
+                    p.stream.synchronize()
+                te = time.perf_counter()
+                lat.append(te - ts)
+                weights.append(active)
+            else:
+                # the host runs ahead; each pool's tick is timed on the GPU
+                te = time.perf_counter()
+                launched = [(p, *p.launch_step(self.d_msgs, timing=True)) for p in busy]
+                pending_ev.extend((ev, len(act)) for _, act, _, ev in launched)
+                if len(pending_ev) > 4 * RING * len(self.pools):
+                    self._drain(pending_ev, lat, weights, keep=RING * len(self.pools))
             steps_done += active
-            msgs_done += sum(m for _, _, m in launched)
+            msgs_done += sum(m for _, _, m, _ in launched)
             if self.collect:
                 self._record(episodes, launched)
             now_after = (te - t0) if clock == "wall" else float(tick)
-            for p, act, _ in launched:
+            for p, act, _, _ in launched:
                 p.step[act] += 1
                 for s in act[p.step[act] >= p.n_steps[act]]:
                     ep = episodes[int(p.ep[s])]
@@ -227,6 +259,8 @@ class Server:
             tick += 1
             if max_ticks is not None and tick >= max_ticks:
                 break
+        torch.cuda.synchronize()
+        self._drain(pending_ev, lat, weights, keep=0)
         wall = time.perf_counter() - t0
         lat_ms = np.repeat(np.asarray(lat) * 1e3, weights) if lat else np.zeros(1)
         waits = [e.admitted - e.arrival for e in episodes if not math.isnan(e.admitted)]
@@ -242,8 +276,17 @@ class Server:
                 "max_active": max_active, "max_hbm_bytes_admitted": max_used,
                 "queue": queue_len}
 
+    @staticmethod
+    def _drain(pending_ev, lat, weights, keep):
+        """Turn completed per-pool tick events into step latencies (seconds)."""
+        while len(pending_ev) > keep:
+            (a, b), n = pending_ev.pop(0)
+            b.synchronize()
+            lat.append(a.elapsed_time(b) / 1e3)
+            weights.append(n)
+
     def _record(self, episodes, launched):
-        for p, act, _ in launched:
+        for p, act, _, _ in launched:
             lv = [x.cpu().numpy() for x in p.levels]
             tc = p.d_tcount.cpu().numpy()
             for s in act:
