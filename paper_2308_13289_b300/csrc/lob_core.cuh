@@ -23,6 +23,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lob {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -344,6 +346,7 @@ template <int K>
 struct RegBook {
     SideVec<K> s[2];
     static constexpr bool kInRegisters = true;
+    static constexpr bool kGrouped = false;
     // the side itself is modified in place; `tmp` is unused
     template <int X> __device__ __forceinline__ SideVec<K>& acquire(SideVec<K>&) { return s[X]; }
     template <int X> __device__ __forceinline__ void release(const SideVec<K>&, bool) {}
@@ -402,6 +405,7 @@ template <int K>
 struct SmemBook {
     char* base;  // staged book image in shared memory
     static constexpr bool kInRegisters = false;
+    static constexpr bool kGrouped = false;
     template <int X> __device__ __forceinline__ char* side() const { return base + X * Geo<K>::SIDE_BYTES; }
     // the lane's slots are moved through `tmp` and written back on release
     template <int X> __device__ __forceinline__ SideVec<K>& acquire(SideVec<K>& tmp)
@@ -425,15 +429,24 @@ struct SmemBook {
     __device__ __forceinline__ void to_image(char*) const {}
 };
 
-// Books whose two sides fit in registers (2 sides x 6 words x K per lane) stay
-// there for the whole stream; the largest capacity works in shared memory.
+// GroupBook: the book stays in shared memory and the add / cancel / match
+// operations walk each lane's slots in groups of four, group g of lane l
+// holding slots g*128 + 4*l + (0..3) ("group-striped": 128-bit accesses of a
+// group are conflict-free), in a loop that is not unrolled, touching only the
+// fields and groups an operation needs.  Code size and per-group cost do not
+// grow with K.  Other code may still use acquire/release (blocked mapping):
+// both mappings place slot s at index s of each field array.
+template <int K>
+struct GroupBook : SmemBook<K> {
+    static constexpr bool kGrouped = true;
+};
+
+// Books whose two sides fit in registers cheaply (K <= 4: 2 sides x 6 words x
+// 4 per lane) stay there for a whole stream; larger capacities work in shared
+// memory, group by group.
 template <int K>
 struct BookPolicy {
-    using type = RegBook<K>;
-};
-template <>
-struct BookPolicy<16> {
-    using type = SmemBook<16>;
+    using type = typename std::conditional<(K <= 4), RegBook<K>, GroupBook<K>>::type;
 };
 
 __device__ __forceinline__ int64_t warp_sum64(int64_t x)
@@ -461,6 +474,16 @@ struct Tally {
 
 // ------------------------------------------------------------ book operations
 
+struct TradeSink;
+template <int K, int X>
+__device__ __noinline__ void g_add_order(char*, int&, int, int, int32_t, int32_t, int32_t, int32_t, int32_t,
+                            int32_t, Tally&);
+template <int K, int X>
+__device__ __noinline__ void g_cancel_order(char*, int&, int32_t, int32_t, Tally&);
+template <int K, int Y, class Obs>
+__device__ __noinline__ int32_t g_match_order(char*, int&, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t,
+                                 TradeSink&, Tally&, Obs&);
+
 // Add the remaining quantity Q as one new order (Sec. 4.1 item 1, Sec. 4.2
 // item 1) at the back of its price level on side X, with the full-side rule:
 // when the side already holds `cap` orders the worst one is evicted if the new
@@ -471,6 +494,10 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
                                           int32_t oid, int32_t tid, int32_t tlo, int32_t thi,
                                           Tally& ctr)
 {
+    if constexpr (Book::kGrouped) {
+        g_add_order<K, X>(bk.template side<X>(), n, cap, rule, P, Q, oid, tid, tlo, thi, ctr);
+        return;
+    }
     const int l = lane_id();
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<X>(tmp);
@@ -507,6 +534,10 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
 template <int K, int X, class Book>
 __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int32_t Q, Tally& ctr)
 {
+    if constexpr (Book::kGrouped) {
+        g_cancel_order<K, X>(bk.template side<X>(), n, oid, Q, ctr);
+        return;
+    }
     const int l = lane_id();
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<X>(tmp);
@@ -614,6 +645,9 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
                                                int32_t tid_a, int32_t tlo, int32_t thi,
                                                TradeSink& ts, Tally& ctr, Obs& obs)
 {
+    if constexpr (Book::kGrouped)
+        return g_match_order<K, Y, Obs>(bk.template side<Y>(), n, P, Q, oid_a, tid_a, tlo, thi,
+                                        ts, ctr, obs);
     const int l = lane_id();
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<Y>(tmp);
@@ -711,6 +745,311 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
         bk.template set_qty<Y>(0, 0, 0, v.q[0]);
     }
     return Q - F;
+}
+
+
+// Warp exclusive prefix and total of the lane values (saturating at INT32_MAX:
+// exact wherever the running total is below Q <= INT32_MAX, which is all that
+// the fills depend on).
+static __device__ __noinline__ uint2 warp_scan_sat(uint32_t acc)
+{
+    const int l = lane_id();
+    uint32_t incl = acc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if (l >= d) incl = sat_add(incl, t);
+    }
+    uint32_t excl = __shfl_up_sync(kFull, incl, 1);
+    if (l == 0) excl = 0;
+    return make_uint2(excl, __shfl_sync(kFull, incl, 31));
+}
+
+// ------------------------------------------------------- grouped operations
+//
+// GroupBook operations: lane l's group g = slots g*128 + 4*l + (0..3).
+
+__device__ __forceinline__ int4 lds4(const int32_t* a) { return *reinterpret_cast<const int4*>(a); }
+__device__ __forceinline__ void sts4(int32_t* a, int4 v) { *reinterpret_cast<int4*>(a) = v; }
+
+struct Q64 { int64_t x, y, z, w; };
+__device__ __forceinline__ Q64 lds8(const int64_t* a)
+{
+    const longlong2 u = reinterpret_cast<const longlong2*>(a)[0];
+    const longlong2 v = reinterpret_cast<const longlong2*>(a)[1];
+    return Q64{u.x, u.y, v.x, v.y};
+}
+__device__ __forceinline__ void sts8(int64_t* a, Q64 q)
+{
+    reinterpret_cast<longlong2*>(a)[0] = make_longlong2(q.x, q.y);
+    reinterpret_cast<longlong2*>(a)[1] = make_longlong2(q.z, q.w);
+}
+
+// New slot s = old slot s-1 for s in (p, n_after), slot p = val.
+template <class T, class V, V (*LD)(const T*), void (*ST)(T*, V)>
+__device__ __forceinline__ void g_shift_in_t(T* arr, int p, int n_after, T val)
+{
+    const int l = lane_id();
+    T carry = 0;  // old slot g*128-1: lane 31's last element of the previous group
+    const int g0 = p >> 7, g1 = (n_after - 1) >> 7;
+#pragma unroll 1
+    for (int g = g0; g <= g1; ++g) {
+        T* a = arr + g * 128 + 4 * l;
+        const V v = LD(a);
+        const T up = __shfl_up_sync(kFull, v.w, 1);
+        const T prev = l == 0 ? carry : up;
+        carry = __shfl_sync(kFull, v.w, 31);
+        const int s = g * 128 + 4 * l;
+        V nv;
+        nv.x = s == p ? val : ((s > p && s < n_after) ? prev : v.x);
+        nv.y = s + 1 == p ? val : ((s + 1 > p && s + 1 < n_after) ? v.x : v.y);
+        nv.z = s + 2 == p ? val : ((s + 2 > p && s + 2 < n_after) ? v.y : v.z);
+        nv.w = s + 3 == p ? val : ((s + 3 > p && s + 3 < n_after) ? v.z : v.w);
+        if (s + 3 >= p && s < n_after) ST(a, nv);
+    }
+}
+
+// New slot s = old slot s+1 for s in [p, n-1): slot p leaves.
+template <class T, class V, V (*LD)(const T*), void (*ST)(T*, V)>
+__device__ __forceinline__ void g_shift_out_t(T* arr, int p, int n)
+{
+    const int l = lane_id();
+    T carry = 0;  // old slot (g+1)*128: lane 0's first element of the next group
+    const int last = n - 1;
+    const int g0 = p >> 7, g1 = last >> 7;
+#pragma unroll 1
+    for (int g = g1; g >= g0; --g) {
+        T* a = arr + g * 128 + 4 * l;
+        const V v = LD(a);
+        const T dn = __shfl_down_sync(kFull, v.x, 1);
+        const T next = l == 31 ? carry : dn;
+        carry = __shfl_sync(kFull, v.x, 0);
+        const int s = g * 128 + 4 * l;
+        V nv;
+        nv.x = (s >= p && s < last) ? v.y : v.x;
+        nv.y = (s + 1 >= p && s + 1 < last) ? v.z : v.y;
+        nv.z = (s + 2 >= p && s + 2 < last) ? v.w : v.z;
+        nv.w = (s + 3 >= p && s + 3 < last) ? next : v.w;
+        if (s + 3 >= p && s < last) ST(a, nv);
+    }
+}
+
+// New slot s = old slot s+m for s in [0, n-m): the first m slots leave.
+template <int K, class T, class V, void (*ST)(T*, V)>
+__device__ __forceinline__ void g_drop_front_t(T* arr, int m, int n)
+{
+    constexpr int cmax = 32 * K - 1;
+    const int l = lane_id();
+    const int keep = n - m;
+#pragma unroll 1
+    for (int g = 0; g * 128 < keep; ++g) {
+        const int s = g * 128 + 4 * l;
+        V nv;
+        nv.x = arr[min(s + m, cmax)];
+        nv.y = arr[min(s + 1 + m, cmax)];
+        nv.z = arr[min(s + 2 + m, cmax)];
+        nv.w = arr[min(s + 3 + m, cmax)];
+        __syncwarp();
+        if (s < keep) ST(arr + s, nv);
+        __syncwarp();
+    }
+}
+
+template <int K>
+struct GSide {
+    char* b;
+    __device__ __forceinline__ int32_t* px() const { return reinterpret_cast<int32_t*>(b + Geo<K>::PX); }
+    __device__ __forceinline__ int32_t* qty() const { return reinterpret_cast<int32_t*>(b + Geo<K>::QTY); }
+    __device__ __forceinline__ int32_t* oid() const { return reinterpret_cast<int32_t*>(b + Geo<K>::OID); }
+    __device__ __forceinline__ int32_t* tid() const { return reinterpret_cast<int32_t*>(b + Geo<K>::TID); }
+    __device__ __forceinline__ int64_t* tm() const { return reinterpret_cast<int64_t*>(b + Geo<K>::TM); }
+};
+
+template <int K>
+__device__ __forceinline__ void g_shift_in_all(GSide<K> sd, int p, int n_after, int32_t P, int32_t Q,
+                                               int32_t oid, int32_t tid, int64_t tm)
+{
+    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.px(), p, n_after, P);
+    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.qty(), p, n_after, Q);
+    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.oid(), p, n_after, oid);
+    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.tid(), p, n_after, tid);
+    g_shift_in_t<int64_t, Q64, lds8, sts8>(sd.tm(), p, n_after, tm);
+}
+
+template <int K>
+__device__ __forceinline__ void g_shift_out_all(GSide<K> sd, int p, int n)
+{
+    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.px(), p, n);
+    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.qty(), p, n);
+    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.oid(), p, n);
+    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.tid(), p, n);
+    g_shift_out_t<int64_t, Q64, lds8, sts8>(sd.tm(), p, n);
+}
+
+template <int K, int X>
+__device__ __noinline__ void g_add_order(char* side, int& n, int cap, int rule, int32_t P,
+                                         int32_t Q, int32_t oid, int32_t tid, int32_t tlo,
+                                         int32_t thi, Tally& ctr)
+{
+    const GSide<K> sd{side};
+    const int l = lane_id();
+    int cnt = 0;
+#pragma unroll 1
+    for (int g = 0; g * 128 < n; ++g) {
+        const int4 v = lds4(sd.px() + g * 128 + 4 * l);
+        const int s = g * 128 + 4 * l;
+        cnt += (s < n && at_least<X>(v.x, P)) + (s + 1 < n && at_least<X>(v.y, P)) +
+               (s + 2 < n && at_least<X>(v.z, P)) + (s + 3 < n && at_least<X>(v.w, P));
+    }
+    const int p = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+    const bool full = n >= cap;
+    if (full && (rule != 0 || p >= cap)) {
+        ctr.rejected += 1;
+        ctr.rejected_qty += Q;
+        return;
+    }
+    if (full) {
+        ctr.evicted += 1;
+        ctr.evicted_qty += sd.qty()[cap - 1];
+    }
+    const int n_after = full ? cap : n + 1;
+    const int64_t tm = (int64_t)(((uint64_t)(uint32_t)thi << 32) | (uint32_t)tlo);
+    g_shift_in_all<K>(sd, p, n_after, P, Q, oid, tid, tm);
+    n = n_after;
+    ctr.rested += 1;
+}
+
+template <int K, int X>
+__device__ __noinline__ void g_cancel_order(char* side, int& n, int32_t oid, int32_t Q, Tally& ctr)
+{
+    const GSide<K> sd{side};
+    const int l = lane_id();
+    int p = -1;
+#pragma unroll 1
+    for (int g = 0; g * 128 < n; ++g) {
+        const int4 v = lds4(sd.oid() + g * 128 + 4 * l);
+        const int s = g * 128 + 4 * l;
+        int jj = (s + 3 < n && v.w == oid) ? 3 : -1;
+        jj = (s + 2 < n && v.z == oid) ? 2 : jj;
+        jj = (s + 1 < n && v.y == oid) ? 1 : jj;
+        jj = (s < n && v.x == oid) ? 0 : jj;
+        const unsigned hit = __ballot_sync(kFull, jj >= 0);
+        if (hit) {
+            const int L = __ffs(hit) - 1;
+            p = g * 128 + 4 * L + __shfl_sync(kFull, jj, L);
+            break;
+        }
+    }
+    if (p < 0) return;
+    ctr.cancel_hit += 1;
+    const int32_t q_old = sd.qty()[p];
+    const int32_t q_new = q_old - Q;
+    if (q_new > 0) {
+        __syncwarp();
+        if (l == 0) sd.qty()[p] = q_new;
+        ctr.cancelled_qty += Q;
+        return;
+    }
+    ctr.cancelled_qty += q_old;
+    g_shift_out_all<K>(sd, p, n);
+    n -= 1;
+}
+
+template <int K, int Y, class Obs>
+__device__ __noinline__ int32_t g_match_order(char* side, int& n, int32_t P, int32_t Q,
+                                              int32_t oid_a, int32_t tid_a, int32_t tlo,
+                                              int32_t thi, TradeSink& ts, Tally& ctr, Obs& obs)
+{
+    const GSide<K> sd{side};
+    const int l = lane_id();
+    uint32_t consumed = 0;  // quantity filled so far (warp-uniform)
+    int m = 0, nf = 0;
+    const int64_t count0 = ts.count;
+#pragma unroll 1
+    for (int g = 0; g * 128 < n; ++g) {
+        const int s = g * 128 + 4 * l;
+        const int4 vp = lds4(sd.px() + g * 128 + 4 * l);
+        const int4 vq = lds4(sd.qty() + g * 128 + 4 * l);
+        const int32_t pa[4] = {vp.x, vp.y, vp.z, vp.w};
+        const int32_t qa[4] = {vq.x, vq.y, vq.z, vq.w};
+        uint32_t cq[4], loc[4];
+        uint32_t acc = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool c = s + j < n && at_least<Y>(pa[j], P);
+            cq[j] = c ? (uint32_t)qa[j] : 0u;
+            acc = sat_add(acc, cq[j]);
+            loc[j] = acc;
+        }
+        const uint32_t Qg = (uint32_t)Q - consumed;
+        const unsigned first_crosses = __ballot_sync(kFull, cq[0] != 0u);
+        const uint32_t acc0 = __shfl_sync(kFull, acc, 0);
+        const bool local = acc0 >= Qg || !(first_crosses & 2u);
+        uint32_t excl, total;
+        if (local) {
+            excl = l == 0 ? 0u : Qg;
+            total = acc0;
+        } else {
+            const uint2 et = warp_scan_sat(acc);
+            excl = et.x;
+            total = et.y;
+        }
+        int32_t fill[4];
+        unsigned nfull = 0, nfill = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t before = sat_add(excl, j == 0 ? 0u : loc[j - 1]);
+            const uint32_t room = before < Qg ? Qg - before : 0u;
+            fill[j] = (int32_t)min(cq[j], room);
+            nfull += (cq[j] != 0u && (uint32_t)fill[j] == cq[j]) ? 1u : 0u;
+            nfill += fill[j] > 0 ? 1u : 0u;
+        }
+        int gm, gnf;
+        if (local) {
+            const unsigned packed = __shfl_sync(kFull, nfull | (nfill << 16), 0);
+            gm = (int)(packed & 0xffffu);
+            gnf = (int)(packed >> 16);
+        } else {
+            gm = (int)__reduce_add_sync(kFull, nfull);
+            gnf = (int)__reduce_add_sync(kFull, nfill);
+        }
+        const uint32_t gF = min(total, Qg);
+        if (gnf > 0) {
+            const int4 vo = lds4(sd.oid() + g * 128 + 4 * l);
+            const int4 vt = lds4(sd.tid() + g * 128 + 4 * l);
+            const int32_t oa[4] = {vo.x, vo.y, vo.z, vo.w};
+            const int32_t ta[4] = {vt.x, vt.y, vt.z, vt.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t idx = count0 + s + j;
+                if (fill[j] > 0 && idx < ts.cap) {
+                    int4* dst = reinterpret_cast<int4*>(ts.log + idx);
+                    dst[0] = make_int4(pa[j], fill[j], oid_a, oa[j]);
+                    dst[1] = make_int4(tid_a, ta[j], tlo, thi);
+                }
+            }
+            obs.template on_fills<4>(fill, pa, ta, tid_a);
+            if (fill[0] | fill[1] | fill[2] | fill[3])
+                sts4(sd.qty() + g * 128 + 4 * l,
+                     make_int4(qa[0] - fill[0], qa[1] - fill[1], qa[2] - fill[2], qa[3] - fill[3]));
+        }
+        consumed += gF;
+        m += gm;
+        nf += gnf;
+        if (gm < 128 || consumed >= (uint32_t)Q) break;
+    }
+    __syncwarp();
+    ts.count += nf;
+    ctr.traded_qty += consumed;
+    if (m > 0) {
+        g_drop_front_t<K, int32_t, int4, sts4>(sd.px(), m, n);
+        g_drop_front_t<K, int32_t, int4, sts4>(sd.qty(), m, n);
+        g_drop_front_t<K, int32_t, int4, sts4>(sd.oid(), m, n);
+        g_drop_front_t<K, int32_t, int4, sts4>(sd.tid(), m, n);
+        g_drop_front_t<K, int64_t, Q64, sts8>(sd.tm(), m, n);
+        n -= m;
+    }
+    return Q - (int32_t)consumed;
 }
 
 // Dispatch codes written by the chunk pre-pass (Sec. 4.2: eight type x side
