@@ -476,12 +476,12 @@ struct Tally {
 
 struct TradeSink;
 template <int K, int X>
-__device__ __noinline__ void g_add_order(char*, int&, int, int, int32_t, int32_t, int32_t, int32_t, int32_t,
+__device__ __forceinline__ void g_add_order(char*, int&, int, int, int32_t, int32_t, int32_t, int32_t, int32_t,
                             int32_t, Tally&);
 template <int K, int X>
-__device__ __noinline__ void g_cancel_order(char*, int&, int32_t, int32_t, Tally&);
+__device__ __forceinline__ void g_cancel_order(char*, int&, int32_t, int32_t, Tally&);
 template <int K, int Y, class Obs>
-__device__ __noinline__ int32_t g_match_order(char*, int&, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t,
+__device__ __forceinline__ int32_t g_match_order(char*, int&, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t,
                                  TradeSink&, Tally&, Obs&);
 
 // Add the remaining quantity Q as one new order (Sec. 4.1 item 1, Sec. 4.2
@@ -865,29 +865,89 @@ struct GSide {
     __device__ __forceinline__ int64_t* tm() const { return reinterpret_cast<int64_t*>(b + Geo<K>::TM); }
 };
 
+// One pass over the touched groups moving every field together (the loads of
+// all fields are issued before any shuffle, so their latencies overlap).
 template <int K>
 __device__ __forceinline__ void g_shift_in_all(GSide<K> sd, int p, int n_after, int32_t P, int32_t Q,
                                                int32_t oid, int32_t tid, int64_t tm)
 {
-    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.px(), p, n_after, P);
-    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.qty(), p, n_after, Q);
-    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.oid(), p, n_after, oid);
-    g_shift_in_t<int32_t, int4, lds4, sts4>(sd.tid(), p, n_after, tid);
-    g_shift_in_t<int64_t, Q64, lds8, sts8>(sd.tm(), p, n_after, tm);
+    const int l = lane_id();
+    int32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    int64_t c4 = 0;
+    const int g0 = p >> 7, g1 = (n_after - 1) >> 7;
+#pragma unroll 1
+    for (int g = g0; g <= g1; ++g) {
+        const int o = g * 128 + 4 * l;
+        const int4 a = lds4(sd.px() + o), b = lds4(sd.qty() + o), c = lds4(sd.oid() + o),
+                   d = lds4(sd.tid() + o);
+        const Q64 e = lds8(sd.tm() + o);
+        const int s = o;
+        const bool t0 = s == p, t1 = s + 1 == p, t2 = s + 2 == p, t3 = s + 3 == p;
+        const bool m0 = s > p && s < n_after, m1 = s + 1 > p && s + 1 < n_after,
+                   m2 = s + 2 > p && s + 2 < n_after, m3 = s + 3 > p && s + 3 < n_after;
+        const bool touch = s + 3 >= p && s < n_after;
+#define LOB_SHIFT_IN(V, VAL, CARRY, T, ST, PTR)                                   \
+        {                                                                         \
+            const T up = __shfl_up_sync(kFull, V.w, 1);                           \
+            const T prev = l == 0 ? CARRY : up;                                   \
+            CARRY = __shfl_sync(kFull, V.w, 31);                                  \
+            auto nv = V;                                                          \
+            nv.x = t0 ? VAL : (m0 ? prev : V.x);                                  \
+            nv.y = t1 ? VAL : (m1 ? V.x : V.y);                                   \
+            nv.z = t2 ? VAL : (m2 ? V.y : V.z);                                   \
+            nv.w = t3 ? VAL : (m3 ? V.z : V.w);                                   \
+            if (touch) ST(PTR + o, nv);                                           \
+        }
+        LOB_SHIFT_IN(a, P, c0, int32_t, sts4, sd.px())
+        LOB_SHIFT_IN(b, Q, c1, int32_t, sts4, sd.qty())
+        LOB_SHIFT_IN(c, oid, c2, int32_t, sts4, sd.oid())
+        LOB_SHIFT_IN(d, tid, c3, int32_t, sts4, sd.tid())
+        LOB_SHIFT_IN(e, tm, c4, int64_t, sts8, sd.tm())
+#undef LOB_SHIFT_IN
+    }
 }
 
 template <int K>
 __device__ __forceinline__ void g_shift_out_all(GSide<K> sd, int p, int n)
 {
-    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.px(), p, n);
-    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.qty(), p, n);
-    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.oid(), p, n);
-    g_shift_out_t<int32_t, int4, lds4, sts4>(sd.tid(), p, n);
-    g_shift_out_t<int64_t, Q64, lds8, sts8>(sd.tm(), p, n);
+    const int l = lane_id();
+    int32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    int64_t c4 = 0;
+    const int last = n - 1;
+    const int g0 = p >> 7, g1 = last >> 7;
+#pragma unroll 1
+    for (int g = g1; g >= g0; --g) {
+        const int o = g * 128 + 4 * l;
+        const int4 a = lds4(sd.px() + o), b = lds4(sd.qty() + o), c = lds4(sd.oid() + o),
+                   d = lds4(sd.tid() + o);
+        const Q64 e = lds8(sd.tm() + o);
+        const int s = o;
+        const bool m0 = s >= p && s < last, m1 = s + 1 >= p && s + 1 < last,
+                   m2 = s + 2 >= p && s + 2 < last, m3 = s + 3 >= p && s + 3 < last;
+        const bool touch = s + 3 >= p && s < last;
+#define LOB_SHIFT_OUT(V, CARRY, T, ST, PTR)                                       \
+        {                                                                         \
+            const T dn = __shfl_down_sync(kFull, V.x, 1);                         \
+            const T next = l == 31 ? CARRY : dn;                                  \
+            CARRY = __shfl_sync(kFull, V.x, 0);                                   \
+            auto nv = V;                                                          \
+            nv.x = m0 ? V.y : V.x;                                                \
+            nv.y = m1 ? V.z : V.y;                                                \
+            nv.z = m2 ? V.w : V.z;                                                \
+            nv.w = m3 ? next : V.w;                                               \
+            if (touch) ST(PTR + o, nv);                                           \
+        }
+        LOB_SHIFT_OUT(a, c0, int32_t, sts4, sd.px())
+        LOB_SHIFT_OUT(b, c1, int32_t, sts4, sd.qty())
+        LOB_SHIFT_OUT(c, c2, int32_t, sts4, sd.oid())
+        LOB_SHIFT_OUT(d, c3, int32_t, sts4, sd.tid())
+        LOB_SHIFT_OUT(e, c4, int64_t, sts8, sd.tm())
+#undef LOB_SHIFT_OUT
+    }
 }
 
 template <int K, int X>
-__device__ __noinline__ void g_add_order(char* side, int& n, int cap, int rule, int32_t P,
+__device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rule, int32_t P,
                                          int32_t Q, int32_t oid, int32_t tid, int32_t tlo,
                                          int32_t thi, Tally& ctr)
 {
@@ -920,7 +980,7 @@ __device__ __noinline__ void g_add_order(char* side, int& n, int cap, int rule, 
 }
 
 template <int K, int X>
-__device__ __noinline__ void g_cancel_order(char* side, int& n, int32_t oid, int32_t Q, Tally& ctr)
+__device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, int32_t Q, Tally& ctr)
 {
     const GSide<K> sd{side};
     const int l = lane_id();
@@ -956,7 +1016,7 @@ __device__ __noinline__ void g_cancel_order(char* side, int& n, int32_t oid, int
 }
 
 template <int K, int Y, class Obs>
-__device__ __noinline__ int32_t g_match_order(char* side, int& n, int32_t P, int32_t Q,
+__device__ __forceinline__ int32_t g_match_order(char* side, int& n, int32_t P, int32_t Q,
                                               int32_t oid_a, int32_t tid_a, int32_t tlo,
                                               int32_t thi, TradeSink& ts, Tally& ctr, Obs& obs)
 {
