@@ -82,20 +82,25 @@ class _Pool:
         self.stream = torch.cuda.Stream()
         with torch.cuda.stream(self.stream):
             self.engine = Engine(slots, capacity, trade_capacity, stream=self.stream)
-            self.d_ids = torch.empty(slots, dtype=torch.int32, device="cuda")
-            self.d_start = torch.empty(slots, dtype=torch.int64, device="cuda")
-            self.d_cnt = torch.empty(slots, dtype=torch.int64, device="cuda")
+            # one packed upload per tick: [start | count | ids (int32 pairs)]
+            self.d_pack = torch.empty(3 * slots, dtype=torch.int64, device="cuda")
+            self.d_start = self.d_pack[:slots]
+            self.d_cnt = self.d_pack[slots:2 * slots]
+            self.d_ids = self.d_pack[2 * slots:].view(torch.int32)
             self.levels = [torch.empty((slots, depth), dtype=torch.int32, device="cuda")
                            for _ in range(4)]
             self.d_tcount = torch.empty(slots, dtype=torch.int64, device="cuda")
             self.d_slot = torch.arange(slots, dtype=torch.int32, device="cuda")
         # a ring of pinned staging sets, so the host can run ahead of the GPU;
         # a set is reused only after the event recorded behind its copies
-        self.ring = [dict(ids=torch.empty(slots, dtype=torch.int32).pin_memory(),
-                          start=torch.empty(slots, dtype=torch.int64).pin_memory(),
-                          cnt=torch.empty(slots, dtype=torch.int64).pin_memory(),
-                          used=torch.cuda.Event(), busy=False) for _ in range(RING)]
+        self.ring = []
+        for _ in range(RING):
+            pack = torch.empty(3 * slots, dtype=torch.int64).pin_memory()
+            self.ring.append(dict(pack=pack, np=pack.numpy(), used=torch.cuda.Event(),
+                                  t0=torch.cuda.Event(enable_timing=True),
+                                  t1=torch.cuda.Event(enable_timing=True), busy=False))
         self.ring_pos = 0
+        self.lat = []  # (GPU ms of a timed tick, episodes in it)
         self.free = list(range(slots - 1, -1, -1))
         self.ep = np.full(slots, -1, np.int64)      # episode index in the slot, -1 free
         self.step = np.zeros(slots, np.int64)
@@ -104,6 +109,20 @@ class _Pool:
         self.base = np.zeros(slots, np.int64)
         self.n_active = 0
         self.collect = collect
+
+    def _retire_slot(self, st):
+        """Wait for a staging set's tick to finish and record its GPU time."""
+        st["used"].synchronize()
+        if st.get("timed"):
+            st["t1"].synchronize()
+            self.lat.append((st["t0"].elapsed_time(st["t1"]), st["n"]))
+        st["busy"] = False
+        st["timed"] = False
+
+    def flush(self):
+        for st in self.ring:
+            if st["busy"]:
+                self._retire_slot(st)
 
     def admit(self, idx: int, ep: Episode):
         s = self.free.pop()
@@ -122,20 +141,22 @@ class _Pool:
         st = self.ring[self.ring_pos]
         self.ring_pos = (self.ring_pos + 1) % len(self.ring)
         if st["busy"]:
-            st["used"].synchronize()
-        st["ids"].numpy()[:n] = act
-        st["start"].numpy()[:n] = self.base[act] + self.step[act] * cnt
-        st["cnt"].numpy()[:n] = cnt
+            self._retire_slot(st)
+        sl = self.slots
+        buf = st["np"]
+        buf[:n] = self.base[act] + self.step[act] * cnt
+        buf[sl:sl + n] = cnt
+        buf[2 * sl:].view(np.int32)[:n] = act
         s = ctypes.c_void_p(self.stream.cuda_stream)
         p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
         ev = None
         with torch.cuda.stream(self.stream):
+            st["timed"] = timing
+            st["n"] = n
             if timing:
-                ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                ev = (st["t0"], st["t1"])
                 ev[0].record(self.stream)
-            self.d_ids[:n].copy_(st["ids"][:n], non_blocking=True)
-            self.d_start[:n].copy_(st["start"][:n], non_blocking=True)
-            self.d_cnt[:n].copy_(st["cnt"][:n], non_blocking=True)
+            self.d_pack.copy_(st["pack"], non_blocking=True)
             st["used"].record(self.stream)
             st["busy"] = True
             rc = lib().lob_process_segments(self.engine.h, p(d_msgs), p(self.d_start),
@@ -198,7 +219,6 @@ class Server:
         lat, weights, queue_len = [], [], []
         steps_done = msgs_done = 0
         max_active = max_used = 0
-        pending_ev = []
         tick = 0
         t0 = time.perf_counter()
         while pending or waiting or any(p.n_active for p in self.pools.values()):
@@ -237,9 +257,6 @@ class Server:
                 # the host runs ahead; each pool's tick is timed on the GPU
                 te = time.perf_counter()
                 launched = [(p, *p.launch_step(self.d_msgs, timing=True)) for p in busy]
-                pending_ev.extend((ev, len(act)) for _, act, _, ev in launched)
-                if len(pending_ev) > 4 * RING * len(self.pools):
-                    self._drain(pending_ev, lat, weights, keep=RING * len(self.pools))
             steps_done += active
             msgs_done += sum(m for _, _, m, _ in launched)
             if self.collect:
@@ -260,7 +277,12 @@ class Server:
             if max_ticks is not None and tick >= max_ticks:
                 break
         torch.cuda.synchronize()
-        self._drain(pending_ev, lat, weights, keep=0)
+        for p in self.pools.values():
+            p.flush()
+            for ms, n in p.lat:
+                lat.append(ms / 1e3)
+                weights.append(n)
+            p.lat = []
         wall = time.perf_counter() - t0
         lat_ms = np.repeat(np.asarray(lat) * 1e3, weights) if lat else np.zeros(1)
         waits = [e.admitted - e.arrival for e in episodes if not math.isnan(e.admitted)]
@@ -275,15 +297,6 @@ class Server:
                 "max_queue": max(q for _, q in queue_len) if queue_len else 0,
                 "max_active": max_active, "max_hbm_bytes_admitted": max_used,
                 "queue": queue_len}
-
-    @staticmethod
-    def _drain(pending_ev, lat, weights, keep):
-        """Turn completed per-pool tick events into step latencies (seconds)."""
-        while len(pending_ev) > keep:
-            (a, b), n = pending_ev.pop(0)
-            b.synchronize()
-            lat.append(a.elapsed_time(b) / 1e3)
-            weights.append(n)
 
     def _record(self, episodes, launched):
         for p, act, _, _ in launched:
