@@ -244,7 +244,7 @@ class EnvOracle:
         lib.oracle_env_destroy.argtypes = [vp]
         lib.oracle_env_books.restype = vp
         lib.oracle_env_books.argtypes = [vp]
-        lib.oracle_env_step.argtypes = [vp, vp, vp, vp, i32] + [vp] * 6 + [i32]
+        lib.oracle_env_step.argtypes = [vp, vp, vp, vp, i32] + [vp] * 6 + [i32, vp]
         lib.oracle_env_state.argtypes = [vp, vp, vp]
         self.lib = lib
         self.n, self.depth = n_envs, depth
@@ -261,7 +261,9 @@ class EnvOracle:
             self.lib.oracle_env_destroy(h)
             self.h = None
 
-    def step(self, replay, offsets, draws, step, threads=None):
+    def step(self, replay, offsets, draws, step, threads=None, l1=False):
+        """One step; with l1=True also returns the level-1 state after every data
+        message (int32 [len(replay), 4])."""
         replay = np.ascontiguousarray(replay, dtype=MSG_DTYPE)
         offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         draws = np.ascontiguousarray(draws, dtype=np.uint32)
@@ -269,9 +271,12 @@ class EnvOracle:
         reward = np.empty(n, np.float32)
         lv = [np.empty((n, d), np.int32) for _ in range(4)]
         fills = np.empty((n, 2), np.int64)
+        tr = np.full((len(replay), 4), -7, np.int32) if l1 else None
         self.lib.oracle_env_step(self.h, _p(replay) if len(replay) else None, _p(offsets),
                                  _p(draws), step, _p(reward), *[_p(x) for x in lv], _p(fills),
-                                 threads or default_threads())
+                                 threads or default_threads(), _p(tr) if l1 and len(replay) else None)
+        if l1:
+            return reward, tuple(lv), fills, tr
         return reward, tuple(lv), fills
 
     def state(self):

@@ -627,7 +627,7 @@ static int32_t best_price(Side& sd)
 
 static void env_step_one(EnvEngine& V, int32_t b, const Msg* msgs, int64_t n_msgs, uint32_t draw,
                          int32_t t, float* reward, int32_t* bid_px, int32_t* bid_qty,
-                         int32_t* ask_px, int32_t* ask_qty, int64_t* fills)
+                         int32_t* ask_px, int32_t* ask_qty, int64_t* fills, int32_t* l1)
 {
     Engine& E = V.E;
     const EnvCfg& cfg = V.cfg;
@@ -639,8 +639,11 @@ static void env_step_one(EnvEngine& V, int32_t b, const Msg* msgs, int64_t n_msg
     sums.agent_tid = cfg.agent_tid;
     bk.sums = &sums;
 
-    // 1. replay the step's data messages
-    for (int64_t k = 0; k < n_msgs; ++k) process(E, bk, msgs[k]);
+    // 1. replay the step's data messages (level-1 state after each, Sec. 5.2.1)
+    for (int64_t k = 0; k < n_msgs; ++k) {
+        process(E, bk, msgs[k]);
+        if (l1) level1(bk, l1 + 4 * k);
+    }
     if (n_msgs > 0) es.last_time = msgs[n_msgs - 1].time_ns;
 
     // 2. initial mid-price of the episode (after the first data window)
@@ -753,14 +756,17 @@ void oracle_env_destroy(void* h) { delete (EnvEngine*)h; }
 void* oracle_env_books(void* h) { return &((EnvEngine*)h)->E; }
 
 // One step for every environment: env b replays replay[offsets[b] .. offsets[b+1]).
+// l1 (nullable): level-1 state after every data message, [message][4] indexed
+// like `replay`.
 void oracle_env_step(void* h, const Msg* replay, const int64_t* offsets, const uint32_t* draws,
                      int32_t step, float* reward, int32_t* bid_px, int32_t* bid_qty,
-                     int32_t* ask_px, int32_t* ask_qty, int64_t* fills, int32_t n_threads)
+                     int32_t* ask_px, int32_t* ask_qty, int64_t* fills, int32_t n_threads,
+                     int32_t* l1)
 {
     EnvEngine& V = *(EnvEngine*)h;
     parallel_for(V.E.n_books, n_threads, [&](int32_t b) {
         env_step_one(V, b, replay + offsets[b], offsets[b + 1] - offsets[b], draws[b], step, reward,
-                     bid_px, bid_qty, ask_px, ask_qty, fills);
+                     bid_px, bid_qty, ask_px, ask_qty, fills, l1 ? l1 + 4 * offsets[b] : nullptr);
     });
 }
 

@@ -107,3 +107,14 @@ def test_env_episode_properties():
     assert (s[:, 1] == 2000).mean() > 0.9
     bk = env.books.book()
     assert not (bk["tid"] == 1_000_000).any(), "agent orders left resting after the last step"
+
+
+def test_env_level1_trace_first_step_equals_book_trace():
+    """Before the agent's first order the environment is a plain book: the
+    level-1 trace of step 0's data equals the book oracle's trace."""
+    p = lobgen.make_params(17)
+    m, off = lobgen.generate(p, [100] * 6)
+    env = oracle.EnvOracle(6, 100, 512, n_steps=5)
+    _, _, _, tr = env.step(m, off, lobgen.agent_draws(1, 6, 1)[0], 0, l1=True)
+    o = oracle.Oracle(6, 100, 512)
+    assert np.array_equal(tr, o.process_l1(m, off))
