@@ -286,13 +286,17 @@ int lob_env_reset(lob_env* env, void* stream);
  *   outputs, each [n_run][n_books][...]: d_reward float; d_bid_px, d_bid_qty,
  *   d_ask_px, d_ask_qty int32 [depth]; d_fills int64 [2] = agent quantity and
  *   agent sum of Q*P of the step.
+ *   d_l1 (NULL = off): int32 [n_run][n_books][msgs_per_step][4], the level-1
+ *              state after every data message of the window (best bid price,
+ *              its quantity, best ask price, its quantity; (-1, 0) when empty),
+ *              the per-message augmented state of Sec. 5.2.1; 16-byte aligned.
  * After the call the book's trade log holds the trades of the last step run.
  * Errors: LOB_E_INVAL when a step is outside [0, n_steps) or an argument is
  * bad. */
 int lob_env_run(lob_env* env, const lob_msg_t* d_replay, int64_t stride_env, int32_t step0,
                 int32_t n_run, const uint32_t* d_draws, float* d_reward, int32_t* d_bid_px,
                 int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty, int64_t* d_fills,
-                void* stream);
+                int32_t* d_l1, void* stream);
 
 /* Agent state: int64[n_books][5] = submitted, executed, id counter, last_ask,
  * last data time; double[n_books] = P_init.  Either pointer may be NULL. */

@@ -176,10 +176,10 @@ def lob_env_reset(e, stream=None):
 
 
 def lob_env_run(e, replay, stride_env, step0, n_run, draws, reward, bid_px, bid_qty, ask_px,
-                ask_qty, fills, stream=None):
+                ask_qty, fills, l1=None, stream=None):
     check(lib().lob_env_run(e, _ptr(replay), stride_env, step0, n_run, _ptr(draws), _ptr(reward),
                             _ptr(bid_px), _ptr(bid_qty), _ptr(ask_px), _ptr(ask_qty), _ptr(fills),
-                            _stream(stream)), "lob_env_run")
+                            _ptr(l1), _stream(stream)), "lob_env_run")
 
 
 def lob_env_get_state(e, state, p_init, stream=None):
@@ -300,15 +300,16 @@ class Env:
                     ask_qty=torch.empty((n_run, n, d), dtype=torch.int32, device="cuda"),
                     fills=torch.empty((n_run, n, 2), dtype=torch.int64, device="cuda"))
 
-    def run(self, replay, stride_env, step0, n_run, draws, out=None, row0=0):
+    def run(self, replay, stride_env, step0, n_run, draws, out=None, row0=0, l1=None):
         """Steps step0..step0+n_run-1; draws int32/uint32 [n_run, n]; results go to
-        rows row0.. of `out` (allocated when None)."""
+        rows row0.. of `out` (allocated when None); l1: optional int32
+        [n_run, n, msgs_per_step, 4] level-1 trace of the data messages."""
         if out is None:
             out = self.outputs(n_run)
             row0 = 0
         sl = {k: v[row0:row0 + n_run] for k, v in out.items()}
         lob_env_run(self.h, replay, stride_env, step0, n_run, draws, sl["reward"], sl["bid_px"],
-                    sl["bid_qty"], sl["ask_px"], sl["ask_qty"], sl["fills"], self.stream)
+                    sl["bid_qty"], sl["ask_px"], sl["ask_qty"], sl["fills"], l1, self.stream)
         return out
 
     def state(self):

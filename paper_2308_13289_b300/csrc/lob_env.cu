@@ -62,6 +62,7 @@ struct EnvArgs {
     int32_t *bid_px, *bid_qty, *ask_px, *ask_qty;
     int64_t* fills;
     uint64_t wait_ns;
+    int32_t* l1;  // [n_run][n_envs][msgs_per_step][4] or null
 };
 
 template <int K>
@@ -272,6 +273,14 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                     }
                     apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
                                      hb.y, hb.z, hb.w, ts, tally, obs);
+                    if (phase == 0 && a.l1 != nullptr) {
+                        const int2 lb = level1_side<K, 0>(bk, n_bid);
+                        const int2 la = level1_side<K, 1>(bk, n_ask);
+                        if (l == 0)
+                            reinterpret_cast<int4*>(a.l1)[((int64_t)r * a.n_envs + b) *
+                                                              a.msgs_per_step + i] =
+                                make_int4(lb.x, lb.y, la.x, la.y);
+                    }
                 }
             }
             n_trades += ts.count;
@@ -499,7 +508,7 @@ int lob_env_reset(lob_env* e, void* stream)
 int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32_t step0,
                 int32_t n_run, const uint32_t* d_draws, float* d_reward, int32_t* d_bid_px,
                 int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty, int64_t* d_fills,
-                void* stream)
+                int32_t* d_l1, void* stream)
 {
     if (!e || !d_replay || !d_draws || !d_reward || !d_bid_px || !d_bid_qty || !d_ask_px ||
         !d_ask_qty || !d_fills || n_run < 1 || step0 < 0 || step0 + n_run > e->cfg.n_steps ||
@@ -507,8 +516,8 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
         lob_set_error("lob_env_run: invalid argument (step0=%d n_run=%d)", step0, n_run);
         return LOB_E_INVAL;
     }
-    if (((uintptr_t)d_replay & 15u) != 0) {
-        lob_set_error("lob_env_run: messages must be 16-byte aligned");
+    if (((uintptr_t)d_replay & 15u) != 0 || ((uintptr_t)d_l1 & 15u) != 0) {
+        lob_set_error("lob_env_run: messages and trace must be 16-byte aligned");
         return LOB_E_INVAL;
     }
     lob_ctx* c = e->book;
@@ -546,6 +555,7 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     a.ask_qty = d_ask_qty;
     a.fills = d_fills;
     a.wait_ns = kEnvWaitNs;
+    a.l1 = d_l1;
     const int W = e->warps;
     int grid = (a.n_envs + W - 1) / W;
     const int resident = c->num_sms * e->per_sm;

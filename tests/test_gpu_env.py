@@ -155,3 +155,24 @@ def test_env_argument_errors(eng):
         env.run(d, 50, 3, 3, dr[:3])  # runs past the episode
     with pytest.raises(eng.LobError):
         env.run(d, 10, 0, 1, dr[:1])  # stride shorter than an episode
+
+
+@pytest.mark.parametrize("cap", [100, 500])
+def test_env_level1_trace_matches_oracle(eng, cap):
+    n_env, n_steps, per = 32, 8, 50
+    m, _ = episode_streams(n_env, n_steps, per, 777 + cap)
+    draws = lobgen.agent_draws(8, n_env, n_steps)
+    e = eng.Engine(n_env, cap, 2048)
+    env = eng.Env(e, n_steps=n_steps, msgs_per_step=per, parent_qty=300)
+    l1 = torch.full((n_steps, n_env, per, 4), -7, dtype=torch.int32, device="cuda")
+    out = env.run(eng.messages_to_device(m), n_steps * per, 0, n_steps,
+                  torch.from_numpy(draws.view(np.int32)).cuda(), l1=l1)
+    torch.cuda.synchronize()
+    oenv = oracle.EnvOracle(n_env, cap, 2048, n_steps=n_steps, parent_qty=300)
+    rows = m.reshape(n_env, n_steps, per)
+    g = l1.cpu().numpy()
+    for t in range(n_steps):
+        stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
+        r_, lv, f_, tr = oenv.step(stp, np.arange(0, n_env * per + 1, per), draws[t], t, l1=True)
+        assert np.array_equal(g[t].reshape(-1, 4), tr), t
+        assert out["reward"][t].cpu().numpy().tobytes() == r_.tobytes()
