@@ -113,7 +113,8 @@ class Oracle:
     """n_books independent books; the same call sequence as the engine's C ABI."""
 
     def __init__(self, n_books: int, capacity: int, trade_capacity: int,
-                 overflow_rule: int = 0, append_trades: bool = False, _borrow=None):
+                 overflow_rule: int = 0, append_trades: bool = False, _borrow=None,
+                 snapshot_cancels: bool = False):
         self.lib = _oracle_lib()
         self.n_books, self.capacity, self.trade_capacity = n_books, capacity, trade_capacity
         if _borrow is not None:  # books owned by an EnvOracle
@@ -121,7 +122,8 @@ class Oracle:
             return
         self._owned = True
         self.h = self.lib.oracle_create(n_books, capacity, trade_capacity, overflow_rule,
-                                        1 if append_trades else 0)
+                                        (1 if append_trades else 0) |
+                                        (2 if snapshot_cancels else 0))
         if not self.h:
             raise ValueError("invalid oracle configuration")
 
@@ -236,7 +238,8 @@ class EnvOracle:
     STATE_FIELDS = ["submitted", "executed", "id_counter", "last_ask", "last_time"]
 
     def __init__(self, n_envs, capacity, trade_capacity, n_steps=400, parent_qty=2000,
-                 agent_tid=1_000_000, depth=10, p_init_fallback=10_000, lam=0.0):
+                 agent_tid=1_000_000, depth=10, p_init_fallback=10_000, lam=0.0,
+                 snapshot_cancels=False):
         lib = _oracle_lib()
         vp, i32 = ctypes.c_void_p, ctypes.c_int32
         lib.oracle_env_create.restype = vp
@@ -252,6 +255,8 @@ class EnvOracle:
                                        agent_tid, depth, p_init_fallback, float(lam))
         if not self.h:
             raise ValueError("invalid environment configuration")
+        lib.oracle_env_set_snapshot_cancels.argtypes = [vp, i32]
+        lib.oracle_env_set_snapshot_cancels(self.h, 1 if snapshot_cancels else 0)
         self.books = Oracle(n_envs, capacity, trade_capacity,
                             _borrow=lib.oracle_env_books(self.h))
 

@@ -183,6 +183,7 @@ struct Book {
 struct Engine {
     int32_t n_books, capacity, trade_capacity, overflow_rule;
     bool append_trades;
+    bool init_price_match = false;  // Sec. 5.1.1 cancels of snapshot orders by price
     std::vector<Book> books;
 };
 
@@ -265,12 +266,25 @@ static void add(Engine& E, Book& bk, const Msg& m, int32_t Q)
     bk.counters[C_RESTED] += 1;
 }
 
+constexpr int32_t SNAPSHOT_OID_MAX = -9000;  // orders from a level snapshot: OID <= -9000
+
 // Cancellation (Sec. 4.1 item 2): locate OID on side S, remove the quantity.
-static void cancel(Book& bk, const Msg& m)
+// With the snapshot rule (Sec. 5.1.1) a cancel whose OID is not live falls back
+// to the snapshot order (OID <= -9000) resting at the cancel's price.
+static void cancel(Engine& E, Book& bk, const Msg& m)
 {
     Side& own = bk.side_of(m.side);
     std::deque<Order>* lvl = nullptr;
     Order* o = own.find(m.oid, &lvl);
+    if (!o && E.init_price_match) {
+        auto it = own.levels.find(m.price);
+        if (it != own.levels.end())
+            for (auto& q : it->second)
+                if (q.oid <= SNAPSHOT_OID_MAX) {
+                    o = &q;
+                    break;
+                }
+    }
     if (!o) {
         bk.counters[C_CANCEL_MISS] += 1;
         return;
@@ -279,7 +293,7 @@ static void cancel(Book& bk, const Msg& m)
     int32_t q_new = o->qty - m.qty;
     if (q_new <= 0) {  // Q <= 0 -> the order leaves the book
         bk.counters[C_CANCELLED_QTY] += o->qty;
-        own.erase(m.oid);
+        own.erase(o->oid);
     } else {
         bk.counters[C_CANCELLED_QTY] += m.qty;
         o->qty = q_new;
@@ -311,7 +325,7 @@ static void process(Engine& E, Book& bk, const Msg& m)
     case 2:
     case 3:  // cancel and delete are treated identically
         bk.counters[C_CANCEL] += 1;
-        cancel(bk, m);
+        cancel(E, bk, m);
         break;
     case 4: {  // market: price 0 for a sell, max_int for a buy; drop the rest
         bk.counters[C_MARKET] += 1;
@@ -371,6 +385,7 @@ int oracle_n_counters(void) { return N_COUNTERS; }
 void* oracle_create(int32_t n_books, int32_t capacity, int32_t trade_capacity,
                     int32_t overflow_rule, int32_t append_trades)
 {
+    // append_trades bit 1 selects the snapshot cancel rule (Sec. 5.1.1)
     if (n_books < 0 || capacity < 1 || trade_capacity < 0 || overflow_rule < 0 ||
         overflow_rule > 1)
         return nullptr;
@@ -379,7 +394,8 @@ void* oracle_create(int32_t n_books, int32_t capacity, int32_t trade_capacity,
     E->capacity = capacity;
     E->trade_capacity = trade_capacity;
     E->overflow_rule = overflow_rule;
-    E->append_trades = append_trades != 0;
+    E->append_trades = (append_trades & 1) != 0;
+    E->init_price_match = (append_trades & 2) != 0;
     E->books.resize((size_t)n_books);
     return E;
 }
@@ -768,6 +784,12 @@ void oracle_env_step(void* h, const Msg* replay, const int64_t* offsets, const u
         env_step_one(V, b, replay + offsets[b], offsets[b + 1] - offsets[b], draws[b], step, reward,
                      bid_px, bid_qty, ask_px, ask_qty, fills, l1 ? l1 + 4 * offsets[b] : nullptr);
     });
+}
+
+// Turn the snapshot cancel rule (Sec. 5.1.1) on or off for the environments' books.
+void oracle_env_set_snapshot_cancels(void* h, int32_t on)
+{
+    ((EnvEngine*)h)->E.init_price_match = on != 0;
 }
 
 // per env: submitted, executed, id_counter, last_ask, last_time; and p_init

@@ -20,6 +20,8 @@ from ._abi import LobConfig, LobEnvConfig, LobError, check
 
 OVERFLOW_EVICT, OVERFLOW_REJECT = 0, 1
 FLAG_APPEND_TRADES = 1
+FLAG_SNAPSHOT_CANCELS = 2
+SNAPSHOT_OID_START = -9000  # snapshot orders: OIDs -9000, -9001, ... (Sec. 5.1.1)
 N_COUNTERS = 20
 COUNTERS = ["msgs", "limit", "cancel", "market", "noop", "invalid", "trades", "traded_qty",
             "rested", "rejected", "rejected_qty", "evicted", "evicted_qty", "cancel_hit",
@@ -189,17 +191,51 @@ def lob_env_get_state(e, state, p_init, stream=None):
 
 # ------------------------------------------------------------------ convenience object
 
+def snapshot_books(bid_px, bid_qty, ask_px, ask_qty, capacity, time_ns=0):
+    """Books in the lob_set_book layout built from level snapshots (Sec. 5.1.1):
+    one order per listed level holding the level's whole volume, OIDs -9000,
+    -9001, ... (the bid levels best first, then the ask levels best first),
+    trader id 0, time `time_ns`.  Inputs are int32 [n_books][depth] tensors in
+    the lob_get_levels layout; a level with price <= 0 or quantity <= 0 ends
+    that side.  Returns the dict Engine.set_book takes, on the inputs' device."""
+    sides = [(bid_px, bid_qty), (ask_px, ask_qty)]
+    n, depth = bid_px.shape
+    dev = bid_px.device
+    if capacity < depth:
+        raise ValueError("capacity %d below the snapshot depth %d" % (capacity, depth))
+    shape = (n, 2, capacity)
+    out = {k: torch.full(shape, -1, dtype=torch.int32, device=dev)
+           for k in ("price", "qty", "oid", "tid")}
+    out["time_ns"] = torch.full(shape, -1, dtype=torch.int64, device=dev)
+    out["count"] = torch.zeros((n, 2), dtype=torch.int32, device=dev)
+    base = torch.zeros(n, dtype=torch.int64, device=dev)
+    for s, (px, q) in enumerate(sides):
+        ok = (px > 0) & (q > 0)
+        cnt = torch.cumprod(ok.to(torch.int32), dim=1).sum(dim=1)  # listed levels, in order
+        live = torch.arange(depth, device=dev).unsqueeze(0) < cnt.unsqueeze(1)
+        oid = SNAPSHOT_OID_START - (base.unsqueeze(1) + torch.arange(depth, device=dev))
+        out["price"][:, s, :depth] = torch.where(live, px, -1)
+        out["qty"][:, s, :depth] = torch.where(live, q, -1)
+        out["oid"][:, s, :depth] = torch.where(live, oid.to(torch.int32), -1)
+        out["tid"][:, s, :depth] = torch.where(live, 0, -1)
+        out["time_ns"][:, s, :depth] = torch.where(live, int(time_ns), -1)
+        out["count"][:, s] = cnt.to(torch.int32)
+        base = base + cnt
+    return out
+
+
 class Engine:
     """A lob_ctx with torch-allocated outputs.  All calls run on the current
     torch stream unless `stream` is given."""
 
     def __init__(self, n_books: int, capacity: int, trade_capacity: int,
                  overflow_rule: int = OVERFLOW_EVICT, append_trades: bool = False,
-                 stream=None):
+                 snapshot_cancels: bool = False, stream=None):
         self.n_books, self.capacity, self.trade_capacity = n_books, capacity, trade_capacity
         self.stream = stream
-        self.h = lob_create(n_books, capacity, trade_capacity, overflow_rule,
-                            FLAG_APPEND_TRADES if append_trades else 0, stream)
+        flags = (FLAG_APPEND_TRADES if append_trades else 0) | \
+                (FLAG_SNAPSHOT_CANCELS if snapshot_cancels else 0)
+        self.h = lob_create(n_books, capacity, trade_capacity, overflow_rule, flags, stream)
 
     def close(self):
         if getattr(self, "h", None):
