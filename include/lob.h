@@ -74,10 +74,15 @@ enum {
 };
 
 enum {
-    LOB_FLAG_APPEND_TRADES = 1  /* the trade log of a book keeps growing across
-                                   lob_process_batch calls until lob_clear_trades
-                                   (default: each call restarts the log of the
-                                   books it touches)                            */
+    LOB_FLAG_APPEND_TRADES = 1,   /* the trade log of a book keeps growing across
+                                     lob_process_batch calls until lob_clear_trades
+                                     (default: each call restarts the log of the
+                                     books it touches)                            */
+    LOB_FLAG_SNAPSHOT_CANCELS = 2 /* books initialised from a level snapshot
+                                     (Sec. 5.1.1): snapshot orders carry
+                                     OID <= -9000, and a cancel/delete whose OID
+                                     is not live on its side applies to the
+                                     snapshot order resting at the cancel's price */
 };
 
 typedef struct {

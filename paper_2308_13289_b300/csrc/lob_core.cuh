@@ -31,6 +31,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxK = 16;        // capacity <= 512
 constexpr int kNumCtr = 20;      // per-book counters (order fixed by the C ABI)
 constexpr int32_t kMaxInt = 2147483647;
+constexpr int32_t kSnapshotOidMax = -9000;  // orders from a level snapshot: OID <= -9000
 
 enum : int {
     CTR_MSGS = 0, CTR_LIMIT, CTR_CANCEL, CTR_MARKET, CTR_NOOP, CTR_INVALID, CTR_TRADES,
@@ -479,7 +480,8 @@ template <int K, int X>
 __device__ __forceinline__ void g_add_order(char*, int&, int, int, int32_t, int32_t, int32_t, int32_t, int32_t,
                             int32_t, Tally&);
 template <int K, int X>
-__device__ __forceinline__ void g_cancel_order(char*, int&, int32_t, int32_t, Tally&);
+__device__ __forceinline__ void g_cancel_order(char*, int&, int32_t, int32_t, int32_t, bool,
+                                               Tally&);
 template <int K, int Y, class Obs>
 __device__ __forceinline__ int32_t g_match_order(char*, int&, int32_t, int32_t, int32_t, int32_t, int32_t, int32_t,
                                  TradeSink&, Tally&, Obs&);
@@ -532,10 +534,11 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
 // Cancellation (Sec. 4.1 item 2): locate OID on side X and remove Q from it;
 // the order leaves the book when its quantity drops to 0 or below.
 template <int K, int X, class Book>
-__device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int32_t Q, Tally& ctr)
+__device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int32_t Q, int32_t P,
+                                             bool snap, Tally& ctr)
 {
     if constexpr (Book::kGrouped) {
-        g_cancel_order<K, X>(bk.template side<X>(), n, oid, Q, ctr);
+        g_cancel_order<K, X>(bk.template side<X>(), n, oid, Q, P, snap, ctr);
         return;
     }
     const int l = lane_id();
@@ -545,7 +548,14 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
 #pragma unroll
     for (int j = K - 1; j >= 0; --j)
         if (l * K + j < n && v.oid[j] == oid) jj = j;
-    const unsigned hit = __ballot_sync(kFull, jj >= 0);
+    unsigned hit = __ballot_sync(kFull, jj >= 0);
+    if (hit == 0 && snap) {
+        // snapshot rule: the snapshot order resting at the cancel's price
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j)
+            if (l * K + j < n && v.px[j] == P && v.oid[j] <= kSnapshotOidMax) jj = j;
+        hit = __ballot_sync(kFull, jj >= 0);
+    }
     if (hit == 0) return;  // not live on this side: no-op (counted at the end)
     ctr.cancel_hit += 1;
     const int L = __ffs(hit) - 1;
@@ -980,7 +990,8 @@ __device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rul
 }
 
 template <int K, int X>
-__device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, int32_t Q, Tally& ctr)
+__device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, int32_t Q,
+                                               int32_t P, bool snap, Tally& ctr)
 {
     const GSide<K> sd{side};
     const int l = lane_id();
@@ -998,6 +1009,25 @@ __device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, 
             const int L = __ffs(hit) - 1;
             p = g * 128 + 4 * L + __shfl_sync(kFull, jj, L);
             break;
+        }
+    }
+    if (p < 0 && snap) {
+        // snapshot rule: the snapshot order resting at the cancel's price
+#pragma unroll 1
+        for (int g = 0; g * 128 < n; ++g) {
+            const int4 v = lds4(sd.oid() + g * 128 + 4 * l);
+            const int4 w = lds4(sd.px() + g * 128 + 4 * l);
+            const int s = g * 128 + 4 * l;
+            int jj = (s + 3 < n && w.w == P && v.w <= kSnapshotOidMax) ? 3 : -1;
+            jj = (s + 2 < n && w.z == P && v.z <= kSnapshotOidMax) ? 2 : jj;
+            jj = (s + 1 < n && w.y == P && v.y <= kSnapshotOidMax) ? 1 : jj;
+            jj = (s < n && w.x == P && v.x <= kSnapshotOidMax) ? 0 : jj;
+            const unsigned hit = __ballot_sync(kFull, jj >= 0);
+            if (hit) {
+                const int L = __ffs(hit) - 1;
+                p = g * 128 + 4 * L + __shfl_sync(kFull, jj, L);
+                break;
+            }
         }
     }
     if (p < 0) return;
@@ -1154,7 +1184,7 @@ template <int K, bool kCompact, class Book, class Obs>
 __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, int cap, int rule,
                                               int32_t op, int32_t P, int32_t Q, int32_t oid,
                                               int32_t tid, int32_t tlo, int32_t thi, TradeSink& ts,
-                                              Tally& ctr, Obs& obs)
+                                              Tally& ctr, Obs& obs, bool snap)
 {
     if constexpr (!kCompact) {
         if (op <= OP_LIMIT_ASK) {
@@ -1171,9 +1201,9 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
             }
         } else if (op <= OP_CANCEL_ASK) {  // cancel and delete are treated identically
             if (op == OP_CANCEL_BID)
-                cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
+                cancel_order<K, 0>(bk, n_bid, oid, Q, P, snap, ctr);
             else
-                cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
+                cancel_order<K, 1>(bk, n_ask, oid, Q, P, snap, ctr);
         } else {  // market: price max_int (buy) / 0 (sell), remainder dropped
             int32_t rest = Q;
             if (op == OP_MARKET_BID) {
@@ -1186,9 +1216,9 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
     } else {
         if (op == OP_CANCEL_BID || op == OP_CANCEL_ASK) {  // cancel and delete: identical
             if (op == OP_CANCEL_BID)
-                cancel_order<K, 0>(bk, n_bid, oid, Q, ctr);
+                cancel_order<K, 0>(bk, n_bid, oid, Q, P, snap, ctr);
             else
-                cancel_order<K, 1>(bk, n_ask, oid, Q, ctr);
+                cancel_order<K, 1>(bk, n_ask, oid, Q, P, snap, ctr);
         } else if (op != OP_SKIP) {
             // limit: match, then rest the remainder; market: match at price max_int
             // (buy) / 0 (sell), then drop the remainder

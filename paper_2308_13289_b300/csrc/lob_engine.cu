@@ -88,6 +88,7 @@ struct ProcArgs {
     int32_t cap, rule, trade_cap, append, chunk, pad_;
     uint64_t wait_ns;
     int32_t* l1;  // level-1 trace [message][4], or null
+    int32_t snap;  // LOB_FLAG_SNAPSHOT_CANCELS
 };
 
 template <int K>
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                     nb = mb[2 * i + 3];
                 }
                 apply_message<K, false>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
-                                 hb.z, hb.w, ts, tally, obs);
+                                 hb.z, hb.w, ts, tally, obs, a.snap != 0);
                 if constexpr (kTrace) {
                     const int2 lb = level1_side<K, 0>(bk, n_bid);
                     const int2 la = level1_side<K, 1>(bk, n_ask);
@@ -486,6 +487,7 @@ int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_off
     a.pad_ = 0;
     a.wait_ns = kWaitNs;
     a.l1 = d_l1;
+    a.snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) ? 1 : 0;
     const int W = c->warps_per_cta;
     int grid = (n_active + W - 1) / W;
     const int resident = c->num_sms * c->ctas_per_sm_eff;
@@ -555,7 +557,7 @@ int lob_create(lob_ctx** out, const lob_config_t* cfg, void* stream)
     }
     if (cfg->n_books < 1 || cfg->capacity < 1 || cfg->capacity > 32 * kMaxK ||
         cfg->trade_capacity < 0 || (cfg->overflow_rule != 0 && cfg->overflow_rule != 1) ||
-        (cfg->flags & ~LOB_FLAG_APPEND_TRADES)) {
+        (cfg->flags & ~(LOB_FLAG_APPEND_TRADES | LOB_FLAG_SNAPSHOT_CANCELS))) {
         lob_set_error("lob_create: invalid configuration (n_books=%d capacity=%d "
                       "trade_capacity=%d overflow_rule=%d flags=%d)",
                       cfg->n_books, cfg->capacity, cfg->trade_capacity, cfg->overflow_rule,
@@ -1025,6 +1027,7 @@ extern "C" int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t
     a.pad_ = 0;
     a.wait_ns = kWaitNs;
     a.l1 = nullptr;
+    a.snap = 0;
     const int W = static_warps(K);
     int grid = (n_books + W - 1) / W;
     const int resident = s->num_sms * s->per_sm[k_index(K)];

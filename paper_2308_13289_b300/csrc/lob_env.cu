@@ -63,6 +63,7 @@ struct EnvArgs {
     int64_t* fills;
     uint64_t wait_ns;
     int32_t* l1;  // [n_run][n_envs][msgs_per_step][4] or null
+    int32_t snap;  // LOB_FLAG_SNAPSHOT_CANCELS
 };
 
 template <int K>
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                         nb = src[2 * i + 3];
                     }
                     apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
-                                     hb.y, hb.z, hb.w, ts, tally, obs);
+                                     hb.y, hb.z, hb.w, ts, tally, obs, a.snap != 0);
                     if (phase == 0 && a.l1 != nullptr) {
                         const int2 lb = level1_side<K, 0>(bk, n_bid);
                         const int2 la = level1_side<K, 1>(bk, n_ask);
@@ -556,6 +557,7 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     a.fills = d_fills;
     a.wait_ns = kEnvWaitNs;
     a.l1 = d_l1;
+    a.snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) ? 1 : 0;
     const int W = e->warps;
     int grid = (a.n_envs + W - 1) / W;
     const int resident = c->num_sms * e->per_sm;
