@@ -989,6 +989,31 @@ __device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rul
     ctr.rested += 1;
 }
 
+// Snapshot rule (Sec. 5.1.1): slot of the earliest order with OID <= -9000
+// resting at price P, or -1.  Out of line: it runs only on a cancel miss.
+template <int K>
+__device__ __noinline__ int g_find_snapshot(const char* side, int n, int32_t P)
+{
+    const GSide<K> sd{const_cast<char*>(side)};
+    const int l = lane_id();
+#pragma unroll 1
+    for (int g = 0; g * 128 < n; ++g) {
+        const int4 v = lds4(sd.oid() + g * 128 + 4 * l);
+        const int4 w = lds4(sd.px() + g * 128 + 4 * l);
+        const int s = g * 128 + 4 * l;
+        int jj = (s + 3 < n && w.w == P && v.w <= kSnapshotOidMax) ? 3 : -1;
+        jj = (s + 2 < n && w.z == P && v.z <= kSnapshotOidMax) ? 2 : jj;
+        jj = (s + 1 < n && w.y == P && v.y <= kSnapshotOidMax) ? 1 : jj;
+        jj = (s < n && w.x == P && v.x <= kSnapshotOidMax) ? 0 : jj;
+        const unsigned hit = __ballot_sync(kFull, jj >= 0);
+        if (hit) {
+            const int L = __ffs(hit) - 1;
+            return g * 128 + 4 * L + __shfl_sync(kFull, jj, L);
+        }
+    }
+    return -1;
+}
+
 template <int K, int X>
 __device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, int32_t Q,
                                                int32_t P, bool snap, Tally& ctr)
@@ -1011,25 +1036,7 @@ __device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, 
             break;
         }
     }
-    if (p < 0 && snap) {
-        // snapshot rule: the snapshot order resting at the cancel's price
-#pragma unroll 1
-        for (int g = 0; g * 128 < n; ++g) {
-            const int4 v = lds4(sd.oid() + g * 128 + 4 * l);
-            const int4 w = lds4(sd.px() + g * 128 + 4 * l);
-            const int s = g * 128 + 4 * l;
-            int jj = (s + 3 < n && w.w == P && v.w <= kSnapshotOidMax) ? 3 : -1;
-            jj = (s + 2 < n && w.z == P && v.z <= kSnapshotOidMax) ? 2 : jj;
-            jj = (s + 1 < n && w.y == P && v.y <= kSnapshotOidMax) ? 1 : jj;
-            jj = (s < n && w.x == P && v.x <= kSnapshotOidMax) ? 0 : jj;
-            const unsigned hit = __ballot_sync(kFull, jj >= 0);
-            if (hit) {
-                const int L = __ffs(hit) - 1;
-                p = g * 128 + 4 * L + __shfl_sync(kFull, jj, L);
-                break;
-            }
-        }
-    }
+    if (p < 0 && snap) p = g_find_snapshot<K>(side, n, P);
     if (p < 0) return;
     ctr.cancel_hit += 1;
     const int32_t q_old = sd.qty()[p];

@@ -73,7 +73,9 @@ __host__ __device__ constexpr int env_warp_smem(int chunk)
            128 * 128;
 }
 
-template <int K>
+// kTrace: the kernel also writes the level-1 state after every data message
+// (a separate instantiation, so the untraced loop carries none of that code).
+template <int K, bool kTrace>
 __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
 {
     using Book = typename BookPolicy<K>::type;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                     }
                     apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
                                      hb.y, hb.z, hb.w, ts, tally, obs, a.snap != 0);
-                    if (phase == 0 && a.l1 != nullptr) {
+                    if (kTrace && phase == 0) {
                         const int2 lb = level1_side<K, 0>(bk, n_bid);
                         const int2 la = level1_side<K, 1>(bk, n_ask);
                         if (l == 0)
@@ -376,15 +378,19 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
     }
 }
 
-const void* env_kernel(int K)
+const void* env_kernel(int K, bool trace)
 {
+#define LOB_ENV_K(k)                                                                   \
+    return trace ? reinterpret_cast<const void*>(&k_env<k, true>)                     \
+                 : reinterpret_cast<const void*>(&k_env<k, false>)
     switch (K) {
-    case 1: return reinterpret_cast<const void*>(&k_env<1>);
-    case 2: return reinterpret_cast<const void*>(&k_env<2>);
-    case 4: return reinterpret_cast<const void*>(&k_env<4>);
-    case 8: return reinterpret_cast<const void*>(&k_env<8>);
-    default: return reinterpret_cast<const void*>(&k_env<16>);
+    case 1: LOB_ENV_K(1);
+    case 2: LOB_ENV_K(2);
+    case 4: LOB_ENV_K(4);
+    case 8: LOB_ENV_K(8);
+    default: LOB_ENV_K(16);
     }
+#undef LOB_ENV_K
 }
 
 int env_smem(int K, int chunk)
@@ -460,10 +466,19 @@ int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, vo
         return LOB_E_INVAL;
     }
     if (err == cudaSuccess)
-        err = lob_raise_smem_limit(env_kernel(K), e->smem_per_cta);
+        err = lob_raise_smem_limit(env_kernel(K, false), e->smem_per_cta);
     if (err == cudaSuccess)
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->per_sm, env_kernel(K),
+        err = lob_raise_smem_limit(env_kernel(K, true), e->smem_per_cta);
+    if (err == cudaSuccess) {
+        // both instantiations share the launch shape: take the smaller residency
+        int per_sm_trace = 0;
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->per_sm, env_kernel(K, false),
                                                             32 * e->warps, e->smem_per_cta);
+        if (err == cudaSuccess)
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm_trace, env_kernel(K, true), 32 * e->warps, e->smem_per_cta);
+        if (err == cudaSuccess && per_sm_trace < e->per_sm) e->per_sm = per_sm_trace;
+    }
     if (err == cudaSuccess)
         err = cudaMalloc(&e->d_state, sizeof(EnvStateDev) * (size_t)book->cfg.n_books);
     if (err != cudaSuccess) {
@@ -563,7 +578,8 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     const int resident = c->num_sms * e->per_sm;
     if (grid > resident) grid = resident;
     void* args[] = {&a};
-    cudaError_t err = cudaLaunchKernel(env_kernel(c->K), dim3(grid), dim3(32 * W), args,
+    cudaError_t err = cudaLaunchKernel(env_kernel(c->K, d_l1 != nullptr), dim3(grid),
+                                       dim3(32 * W), args,
                                        (size_t)e->smem_per_cta, (cudaStream_t)stream);
     if (err != cudaSuccess) return lob_cuda_fail(err, "lob_env_run launch");
     c->launches += 1;
