@@ -239,20 +239,22 @@ class EnvOracle:
 
     def __init__(self, n_envs, capacity, trade_capacity, n_steps=400, parent_qty=2000,
                  agent_tid=1_000_000, depth=10, p_init_fallback=10_000, lam=0.0,
-                 snapshot_cancels=False):
+                 snapshot_cancels=False, passive_ticks=2, tick_size=1):
         lib = _oracle_lib()
         vp, i32 = ctypes.c_void_p, ctypes.c_int32
         lib.oracle_env_create.restype = vp
-        lib.oracle_env_create.argtypes = [i32] * 8 + [ctypes.c_double]
+        lib.oracle_env_create.argtypes = [i32] * 10 + [ctypes.c_double]
         lib.oracle_env_destroy.argtypes = [vp]
         lib.oracle_env_books.restype = vp
         lib.oracle_env_books.argtypes = [vp]
-        lib.oracle_env_step.argtypes = [vp, vp, vp, vp, i32] + [vp] * 6 + [i32, vp]
+        lib.oracle_env_step.argtypes = [vp, vp, vp, vp, vp, i32] + [vp] * 6 + [i32, vp]
+        lib.oracle_env_observe.argtypes = [vp, vp, i32, vp, vp]
         lib.oracle_env_state.argtypes = [vp, vp, vp]
         self.lib = lib
         self.n, self.depth = n_envs, depth
         self.h = lib.oracle_env_create(n_envs, capacity, trade_capacity, n_steps, parent_qty,
-                                       agent_tid, depth, p_init_fallback, float(lam))
+                                       agent_tid, depth, p_init_fallback, passive_ticks,
+                                       tick_size, float(lam))
         if not self.h:
             raise ValueError("invalid environment configuration")
         lib.oracle_env_set_snapshot_cancels.argtypes = [vp, i32]
@@ -266,19 +268,26 @@ class EnvOracle:
             self.lib.oracle_env_destroy(h)
             self.h = None
 
-    def step(self, replay, offsets, draws, step, threads=None, l1=False):
-        """One step; with l1=True also returns the level-1 state after every data
-        message (int32 [len(replay), 4])."""
+    def step(self, replay, offsets, draws, step, threads=None, l1=False, actions=None):
+        """One step; the agent acts from `draws` (uint32 [n]) or, when given,
+        from `actions` (float32 [n, 4]: sizes at the far-touch, mid, near-touch
+        and passive prices).  With l1=True also returns the level-1 state after
+        every data message (int32 [len(replay), 4])."""
         replay = np.ascontiguousarray(replay, dtype=MSG_DTYPE)
         offsets = np.ascontiguousarray(offsets, dtype=np.int64)
-        draws = np.ascontiguousarray(draws, dtype=np.uint32)
+        draws = None if draws is None else np.ascontiguousarray(draws, dtype=np.uint32)
+        act = None if actions is None else np.ascontiguousarray(actions, dtype=np.float32)
+        if act is not None:
+            assert act.shape == (self.n, 4)
         n, d = self.n, self.depth
         reward = np.empty(n, np.float32)
         lv = [np.empty((n, d), np.int32) for _ in range(4)]
         fills = np.empty((n, 2), np.int64)
         tr = np.full((len(replay), 4), -7, np.int32) if l1 else None
         self.lib.oracle_env_step(self.h, _p(replay) if len(replay) else None, _p(offsets),
-                                 _p(draws), step, _p(reward), *[_p(x) for x in lv], _p(fills),
+                                 None if draws is None else _p(draws),
+                                 None if act is None else _p(act), step, _p(reward),
+                                 *[_p(x) for x in lv], _p(fills),
                                  threads or default_threads(), _p(tr) if l1 and len(replay) else None)
         if l1:
             return reward, tuple(lv), fills, tr
@@ -289,3 +298,12 @@ class EnvOracle:
         p0 = np.empty(self.n, np.float64)
         self.lib.oracle_env_state(self.h, _p(out), _p(p0))
         return out, p0
+
+    def observe(self, l1, msgs_per_step, t_init):
+        """Observation after the most recent step (see oracle_env_observe):
+        l1 int32 [n, M, 4] (that step's trace), t_init int64 [n]."""
+        tr = np.ascontiguousarray(l1, dtype=np.int32).reshape(self.n, msgs_per_step, 4)
+        t0 = np.ascontiguousarray(t_init, dtype=np.int64)
+        obs = np.empty((self.n, 6 * msgs_per_step + 8), np.float32)
+        self.lib.oracle_env_observe(self.h, _p(tr), msgs_per_step, _p(t0), _p(obs))
+        return obs

@@ -40,6 +40,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <deque>
 #include <functional>
 #include <map>
@@ -620,6 +621,7 @@ namespace oracle {
 
 struct EnvCfg {
     int32_t n_steps, parent_qty, agent_tid, depth, p_init_fallback;
+    int32_t passive_ticks, tick_size;  // P_passive = P_ask + n x ticksize (Sec. 5.2.2)
     double lambda;
 };
 
@@ -641,9 +643,40 @@ static int32_t best_price(Side& sd)
     return sd.best().price;
 }
 
+// Order size from one continuous action component (Sec. 5.2.3): the whole
+// part of the component, nothing for a component below one share (or NaN),
+// at most what is left of the task.
+static int64_t action_qty(float a, int64_t remaining)
+{
+    const double x = (double)a;
+    if (!(x >= 1.0) || remaining <= 0) return 0;
+    const double w = std::floor(x);
+    return w >= (double)remaining ? remaining : (int64_t)w;
+}
+
+// The four prices of the action space for a sell task (Sec. 5.2.3): far touch
+// = best bid, mid (rounded up to the tick grid for a sell), near touch = best
+// ask, passive = best ask + n ticks.  A price whose side is missing is -1.
+static void action_prices(Book& bk, int32_t passive_ticks, int32_t tick, int32_t out[4])
+{
+    const bool hb = !bk.bids.empty(), ha = !bk.asks.empty();
+    const int64_t pb = hb ? best_price(bk.bids) : -1, pa = ha ? best_price(bk.asks) : -1;
+    out[0] = (int32_t)pb;
+    if (hb && ha) {
+        const int64_t two_t = 2 * (int64_t)tick;
+        out[1] = (int32_t)((pb + pa + two_t - 1) / two_t * tick);  // smallest grid price >= mid
+    } else {
+        out[1] = (int32_t)(hb ? pb : pa);
+    }
+    out[2] = (int32_t)pa;
+    const int64_t pp = pa + (int64_t)passive_ticks * tick;
+    out[3] = (ha && pp <= INT32_MAX) ? (int32_t)pp : -1;
+}
+
 static void env_step_one(EnvEngine& V, int32_t b, const Msg* msgs, int64_t n_msgs, uint32_t draw,
-                         int32_t t, float* reward, int32_t* bid_px, int32_t* bid_qty,
-                         int32_t* ask_px, int32_t* ask_qty, int64_t* fills, int32_t* l1)
+                         const float* action, int32_t t, float* reward, int32_t* bid_px,
+                         int32_t* bid_qty, int32_t* ask_px, int32_t* ask_qty, int64_t* fills,
+                         int32_t* l1)
 {
     Engine& E = V.E;
     const EnvCfg& cfg = V.cfg;
@@ -689,7 +722,19 @@ static void env_step_one(EnvEngine& V, int32_t b, const Msg* msgs, int64_t n_msg
         es.submitted += qty;
         process(E, bk, m);
     };
-    if (t < cfg.n_steps - 1) {
+    if (t < cfg.n_steps - 1 && action) {
+        // the policy's sizes at the four prices, in the order listed (Sec. 5.2.3)
+        if (!bk.asks.empty()) es.last_ask = best_price(bk.asks);
+        int32_t px[4];
+        action_prices(bk, cfg.passive_ticks, cfg.tick_size, px);
+        int64_t remaining = cfg.parent_qty - es.submitted;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t q = action_qty(action[k], remaining);
+            if (px[k] <= 0 || q <= 0) continue;
+            send(1, px[k], (int32_t)q);
+            remaining -= q;
+        }
+    } else if (t < cfg.n_steps - 1) {
         if (!bk.asks.empty()) es.last_ask = best_price(bk.asks);
         const int64_t remaining = cfg.parent_qty - es.submitted;
         const int64_t steps_left = cfg.n_steps - t;
@@ -748,10 +793,11 @@ extern "C" {
 
 void* oracle_env_create(int32_t n_envs, int32_t capacity, int32_t trade_capacity, int32_t n_steps,
                         int32_t parent_qty, int32_t agent_tid, int32_t depth,
-                        int32_t p_init_fallback, double lambda)
+                        int32_t p_init_fallback, int32_t passive_ticks, int32_t tick_size,
+                        double lambda)
 {
     if (n_envs < 1 || capacity < 1 || trade_capacity < 0 || n_steps < 1 || parent_qty < 0 ||
-        depth < 1)
+        depth < 1 || passive_ticks < 0 || tick_size < 1)
         return nullptr;
     EnvEngine* V = new EnvEngine();
     V->E.n_books = n_envs;
@@ -760,7 +806,8 @@ void* oracle_env_create(int32_t n_envs, int32_t capacity, int32_t trade_capacity
     V->E.overflow_rule = 0;
     V->E.append_trades = false;
     V->E.books.resize((size_t)n_envs);
-    V->cfg = EnvCfg{n_steps, parent_qty, agent_tid, depth, p_init_fallback, lambda};
+    V->cfg = EnvCfg{n_steps, parent_qty, agent_tid, depth, p_init_fallback, passive_ticks,
+                    tick_size, lambda};
     V->st.assign((size_t)n_envs, EnvState());
     for (auto& s : V->st) s.last_ask = p_init_fallback;
     return V;
@@ -772,18 +819,75 @@ void oracle_env_destroy(void* h) { delete (EnvEngine*)h; }
 void* oracle_env_books(void* h) { return &((EnvEngine*)h)->E; }
 
 // One step for every environment: env b replays replay[offsets[b] .. offsets[b+1]).
+// The agent acts from draws[b] (the seeded stand-in), or, when `actions` is
+// given, from the four sizes actions[4b .. 4b+4).
 // l1 (nullable): level-1 state after every data message, [message][4] indexed
 // like `replay`.
 void oracle_env_step(void* h, const Msg* replay, const int64_t* offsets, const uint32_t* draws,
-                     int32_t step, float* reward, int32_t* bid_px, int32_t* bid_qty,
-                     int32_t* ask_px, int32_t* ask_qty, int64_t* fills, int32_t n_threads,
-                     int32_t* l1)
+                     const float* actions, int32_t step, float* reward, int32_t* bid_px,
+                     int32_t* bid_qty, int32_t* ask_px, int32_t* ask_qty, int64_t* fills,
+                     int32_t n_threads, int32_t* l1)
 {
     EnvEngine& V = *(EnvEngine*)h;
     parallel_for(V.E.n_books, n_threads, [&](int32_t b) {
-        env_step_one(V, b, replay + offsets[b], offsets[b + 1] - offsets[b], draws[b], step, reward,
-                     bid_px, bid_qty, ask_px, ask_qty, fills, l1 ? l1 + 4 * offsets[b] : nullptr);
+        env_step_one(V, b, replay + offsets[b], offsets[b + 1] - offsets[b],
+                     draws ? draws[b] : 0u, actions ? actions + 4 * (int64_t)b : nullptr, step,
+                     reward, bid_px, bid_qty, ask_px, ask_qty, fills,
+                     l1 ? l1 + 4 * offsets[b] : nullptr);
     });
+}
+
+// Observation of every environment after its most recent step (Sec. 5.2.2),
+// float32 [n_envs][6M + 8], M = messages per step, in the order the paper
+// lists: best bid prices [M], best ask prices [M], mid prices [M], passive
+// prices [M], spreads [M], current time [s, ns], elapsed time [s, ns], P_init,
+// drift P_mid - P_init, task size, quantity executed, level-1 imbalances
+// Q_ask - Q_bid [M].  l1: that step's level-1 trace, [n_envs][M][4];
+// t_init: each episode's initial time (its first replay record's time).
+// A per-message value that needs a missing side is -1; the drift uses the mid
+// after the step's last data message (0 when it is undefined).
+void oracle_env_observe(void* h, const int32_t* l1, int32_t M, const int64_t* t_init, float* obs)
+{
+    EnvEngine& V = *(EnvEngine*)h;
+    const EnvCfg& cfg = V.cfg;
+    const int64_t row = 6 * (int64_t)M + 8;
+    const int64_t kSec = 1000000000;
+    for (size_t b = 0; b < V.st.size(); ++b) {
+        const EnvState& es = V.st[b];
+        float* o = obs + (int64_t)b * row;
+        double mid_last = -1.0;
+        for (int32_t k = 0; k < M; ++k) {
+            const int32_t* r = l1 + ((int64_t)b * M + k) * 4;
+            const int32_t pb = r[0], qb = r[1], pa = r[2], qa = r[3];
+            const bool hb = pb > 0, ha = pa > 0;
+            double mid = -1.0;
+            if (hb && ha)
+                mid = ((double)pb + (double)pa) / 2.0;
+            else if (hb)
+                mid = (double)pb;
+            else if (ha)
+                mid = (double)pa;
+            const int64_t passive = ha ? (int64_t)pa + (int64_t)cfg.passive_ticks * cfg.tick_size
+                                       : -1;
+            o[k] = (float)pb;
+            o[M + k] = (float)pa;
+            o[2 * M + k] = (float)mid;
+            o[3 * M + k] = (float)passive;
+            o[4 * M + k] = (float)(hb && ha ? (int64_t)pa - pb : -1);
+            o[5 * M + 8 + k] = (float)((int64_t)qa - qb);
+            mid_last = mid;
+        }
+        float* sc = o + 5 * M;
+        const int64_t tc = es.last_time, te = es.last_time - t_init[b];
+        sc[0] = (float)(tc / kSec);
+        sc[1] = (float)(tc % kSec);
+        sc[2] = (float)(te / kSec);
+        sc[3] = (float)(te % kSec);
+        sc[4] = (float)es.p_init;
+        sc[5] = (float)(mid_last >= 0.0 ? mid_last - es.p_init : 0.0);
+        sc[6] = (float)cfg.parent_qty;
+        sc[7] = (float)es.executed;
+    }
 }
 
 // Turn the snapshot cancel rule (Sec. 5.1.1) on or off for the environments' books.
