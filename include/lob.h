@@ -260,7 +260,17 @@ int lob_get_stats(lob_ctx* ctx, int64_t* d_counters, int32_t* d_status, void* st
  * parent_qty - executed at market (Sec. 5.2.5).  Agent orders carry
  * oid 2^30 + counter, tid agent_tid and the time of the step's last data
  * message (Sec. 5.1.3).  Draws are uint32: bits 0-1 = child orders - 1,
- * bits 2+3k..4+3k = action of child k (0..4 = -2..+2 ticks, 5 = market). */
+ * bits 2+3k..4+3k = action of child k (0..4 = -2..+2 ticks, 5 = market).
+ *
+ * Policy actions (Sec. 5.2.3) replace the stand-in when lob_env_run gets
+ * d_actions: four float sizes, placed as limit sells in this order at the far
+ * touch (best bid), the mid rounded up to the tick grid (the one best price
+ * when a side is empty), the near touch (best ask) and the passive price
+ * (best ask + passive_ticks x tick_size), all read from the book after the
+ * step's data messages.  A size is the whole part of its component, none
+ * below 1 or for NaN, at most parent_qty - submitted (taken in that order);
+ * an order whose price needs a missing side is not placed.  The last step
+ * ignores the action and closes out as above. */
 typedef struct {
     int32_t n_steps;          /* episode length                                 */
     int32_t parent_qty;       /* shares the agent sells over the episode         */
@@ -269,6 +279,8 @@ typedef struct {
     int32_t p_init_fallback;  /* initial mid / last_ask when a side is empty     */
     int32_t msgs_per_step;    /* data messages per step, 1..1024                 */
     double lambda;            /* drift weight of eq. rewardfunc                  */
+    int32_t passive_ticks;    /* n of P_passive = P_ask + n x ticksize, >= 0     */
+    int32_t tick_size;        /* price units per tick, >= 1 (Sec. 5.2.2)         */
 } lob_env_config_t;
 
 typedef struct lob_env lob_env;
@@ -287,7 +299,9 @@ int lob_env_reset(lob_env* env, void* stream);
  * books stay in on-chip memory across the steps).  n_run = 1 is one step.
  *   d_replay : data messages, 16-byte aligned; env b's step t window is
  *              d_replay[b*stride_env + t*msgs_per_step ..][0 .. msgs_per_step)
- *   d_draws  : uint32[n_run][n_books] agent draws of those steps
+ *   d_draws  : uint32[n_run][n_books] agent draws of those steps, or NULL
+ *              when d_actions is given
+ *   d_actions: float[n_run][n_books][4] policy sizes (see above), or NULL
  *   outputs, each [n_run][n_books][...]: d_reward float; d_bid_px, d_bid_qty,
  *   d_ask_px, d_ask_qty int32 [depth]; d_fills int64 [2] = agent quantity and
  *   agent sum of Q*P of the step.
@@ -299,9 +313,25 @@ int lob_env_reset(lob_env* env, void* stream);
  * Errors: LOB_E_INVAL when a step is outside [0, n_steps) or an argument is
  * bad. */
 int lob_env_run(lob_env* env, const lob_msg_t* d_replay, int64_t stride_env, int32_t step0,
-                int32_t n_run, const uint32_t* d_draws, float* d_reward, int32_t* d_bid_px,
-                int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty, int64_t* d_fills,
-                int32_t* d_l1, void* stream);
+                int32_t n_run, const uint32_t* d_draws, const float* d_actions, float* d_reward,
+                int32_t* d_bid_px, int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty,
+                int64_t* d_fills, int32_t* d_l1, void* stream);
+
+/* Observation of every environment after its most recent step (Sec. 5.2.2):
+ * d_obs float [n_books][6M + 8], M = msgs_per_step, laid out in the order the
+ * paper lists: best bid prices [M], best ask prices [M], mid prices [M],
+ * passive prices [M], spreads [M], current time [s, ns], elapsed time
+ * [s, ns], P_init, drift P_mid - P_init, task size, quantity executed,
+ * level-1 imbalances Q_ask - Q_bid [M].  The per-message arrays come from
+ * d_l1, that step's level-1 trace (int32 [n_books][M][4] as lob_env_run
+ * writes it; for a multi-step run, the last step's slice); a value that needs
+ * a missing side is -1.  Current time = the step's last data message; elapsed
+ * = current - the time of the episode's first replay record
+ * (d_replay[b*stride_env]); the drift uses the mid after the last data
+ * message (0 when undefined).  Each value is one IEEE round-to-nearest of an
+ * exact integer or half-integer.  d_l1 16-byte aligned. */
+int lob_env_observe(lob_env* env, const lob_msg_t* d_replay, int64_t stride_env,
+                    const int32_t* d_l1, float* d_obs, void* stream);
 
 /* Agent state: int64[n_books][5] = submitted, executed, id counter, last_ask,
  * last data time; double[n_books] = P_init.  Either pointer may be NULL. */

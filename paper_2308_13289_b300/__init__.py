@@ -160,10 +160,10 @@ def lob_process_streams_static(msgs, offsets, n_books, capacity, trade_capacity,
 
 
 def lob_env_create(h, n_steps, parent_qty, agent_tid, depth, p_init_fallback, msgs_per_step,
-                   lam=0.0, stream=None):
+                   lam=0.0, passive_ticks=2, tick_size=1, stream=None):
     e = ctypes.c_void_p()
     cfg = LobEnvConfig(n_steps, parent_qty, agent_tid, depth, p_init_fallback, msgs_per_step,
-                       float(lam))
+                       float(lam), passive_ticks, tick_size)
     check(lib().lob_env_create(ctypes.byref(e), h, ctypes.byref(cfg), _stream(stream)),
           "lob_env_create")
     return e
@@ -178,10 +178,16 @@ def lob_env_reset(e, stream=None):
 
 
 def lob_env_run(e, replay, stride_env, step0, n_run, draws, reward, bid_px, bid_qty, ask_px,
-                ask_qty, fills, l1=None, stream=None):
-    check(lib().lob_env_run(e, _ptr(replay), stride_env, step0, n_run, _ptr(draws), _ptr(reward),
-                            _ptr(bid_px), _ptr(bid_qty), _ptr(ask_px), _ptr(ask_qty), _ptr(fills),
-                            _ptr(l1), _stream(stream)), "lob_env_run")
+                ask_qty, fills, l1=None, actions=None, stream=None):
+    check(lib().lob_env_run(e, _ptr(replay), stride_env, step0, n_run, _ptr(draws),
+                            _ptr(actions), _ptr(reward), _ptr(bid_px), _ptr(bid_qty),
+                            _ptr(ask_px), _ptr(ask_qty), _ptr(fills), _ptr(l1), _stream(stream)),
+          "lob_env_run")
+
+
+def lob_env_observe(e, replay, stride_env, l1, obs, stream=None):
+    check(lib().lob_env_observe(e, _ptr(replay), stride_env, _ptr(l1), _ptr(obs),
+                                _stream(stream)), "lob_env_observe")
 
 
 def lob_env_get_state(e, state, p_init, stream=None):
@@ -307,11 +313,12 @@ class Env:
     """Execution environments over the books of an Engine (see lob_env_* in lob.h)."""
 
     def __init__(self, engine: "Engine", n_steps=400, parent_qty=2000, agent_tid=1_000_000,
-                 depth=10, p_init_fallback=10_000, msgs_per_step=100, lam=0.0, stream=None):
+                 depth=10, p_init_fallback=10_000, msgs_per_step=100, lam=0.0, passive_ticks=2,
+                 tick_size=1, stream=None):
         self.engine, self.n, self.depth, self.stream = engine, engine.n_books, depth, stream
         self.n_steps, self.msgs_per_step = n_steps, msgs_per_step
         self.h = lob_env_create(engine.h, n_steps, parent_qty, agent_tid, depth, p_init_fallback,
-                                msgs_per_step, lam, stream)
+                                msgs_per_step, lam, passive_ticks, tick_size, stream)
 
     def close(self):
         if getattr(self, "h", None):
@@ -336,17 +343,31 @@ class Env:
                     ask_qty=torch.empty((n_run, n, d), dtype=torch.int32, device="cuda"),
                     fills=torch.empty((n_run, n, 2), dtype=torch.int64, device="cuda"))
 
-    def run(self, replay, stride_env, step0, n_run, draws, out=None, row0=0, l1=None):
-        """Steps step0..step0+n_run-1; draws int32/uint32 [n_run, n]; results go to
-        rows row0.. of `out` (allocated when None); l1: optional int32
-        [n_run, n, msgs_per_step, 4] level-1 trace of the data messages."""
+    def run(self, replay, stride_env, step0, n_run, draws, out=None, row0=0, l1=None,
+            actions=None):
+        """Steps step0..step0+n_run-1; the agent acts from draws (int32/uint32
+        [n_run, n], the seeded stand-in) or, with draws=None, from actions
+        (float32 [n_run, n, 4], sizes at the far-touch, mid, near-touch and
+        passive prices); results go to rows row0.. of `out` (allocated when
+        None); l1: optional int32 [n_run, n, msgs_per_step, 4] level-1 trace of
+        the data messages."""
         if out is None:
             out = self.outputs(n_run)
             row0 = 0
         sl = {k: v[row0:row0 + n_run] for k, v in out.items()}
         lob_env_run(self.h, replay, stride_env, step0, n_run, draws, sl["reward"], sl["bid_px"],
-                    sl["bid_qty"], sl["ask_px"], sl["ask_qty"], sl["fills"], l1, self.stream)
+                    sl["bid_qty"], sl["ask_px"], sl["ask_qty"], sl["fills"], l1, actions,
+                    self.stream)
         return out
+
+    def observe(self, replay, stride_env, l1, obs=None):
+        """Observation after the most recent step, float32 [n, 6M + 8]; l1 is
+        that step's trace, int32 [n, msgs_per_step, 4]."""
+        if obs is None:
+            obs = torch.empty((self.n, 6 * self.msgs_per_step + 8), dtype=torch.float32,
+                              device="cuda")
+        lob_env_observe(self.h, replay, stride_env, l1, obs, self.stream)
+        return obs
 
     def state(self):
         st = torch.empty((self.n, 5), dtype=torch.int64, device="cuda")

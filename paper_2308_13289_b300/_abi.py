@@ -19,7 +19,8 @@ class LobConfig(ctypes.Structure):
 
 class LobEnvConfig(ctypes.Structure):
     _fields_ = [("n_steps", i32), ("parent_qty", i32), ("agent_tid", i32), ("depth", i32),
-                ("p_init_fallback", i32), ("msgs_per_step", i32), ("lam", ctypes.c_double)]
+                ("p_init_fallback", i32), ("msgs_per_step", i32), ("lam", ctypes.c_double),
+                ("passive_ticks", i32), ("tick_size", i32)]
 
 
 # name -> (restype, argtypes); every symbol of include/lob.h
@@ -44,7 +45,8 @@ SIGNATURES = {
     "lob_env_create": (ctypes.c_int, [ctypes.POINTER(vp), vp, ctypes.POINTER(LobEnvConfig), vp]),
     "lob_env_destroy": (ctypes.c_int, [vp]),
     "lob_env_reset": (ctypes.c_int, [vp, vp]),
-    "lob_env_run": (ctypes.c_int, [vp, vp, i64, i32, i32] + [vp] * 8 + [vp]),
+    "lob_env_run": (ctypes.c_int, [vp, vp, i64, i32, i32] + [vp] * 9 + [vp]),
+    "lob_env_observe": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
     "lob_env_get_state": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_last_error": (ctypes.c_char_p, []),
     "lob_abi_version": (ctypes.c_int, []),

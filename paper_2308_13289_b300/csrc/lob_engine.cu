@@ -543,7 +543,7 @@ static int configure_launch(lob_ctx* c, int W, int chunk, int ctas_per_sm)
 
 extern "C" {
 
-int lob_abi_version(void) { return 1; }
+int lob_abi_version(void) { return 2; }
 
 const char* lob_last_error(void) { return g_err.c_str(); }
 

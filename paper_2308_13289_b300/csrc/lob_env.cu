@@ -64,6 +64,8 @@ struct EnvArgs {
     uint64_t wait_ns;
     int32_t* l1;  // [n_run][n_envs][msgs_per_step][4] or null
     int32_t snap;  // LOB_FLAG_SNAPSHOT_CANCELS
+    const float* actions;  // [n_run][n_envs][4] policy sizes, or null (stand-in draws)
+    int32_t passive_ticks, tick;
 };
 
 template <int K>
@@ -212,7 +214,38 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                         else
                             es.p_init = (double)a.p_fallback;
                     }
-                    if (t < a.n_steps - 1) {
+                    if (t < a.n_steps - 1 && a.actions != nullptr) {
+                        // policy sizes at the four prices (Sec. 5.2.3), prices read
+                        // once from the book after the data messages
+                        if (n_ask > 0) es.last_ask = bk.template best_px<1>();
+                        const float* av = a.actions + ((int64_t)r * a.n_envs + b) * 4;
+                        const int64_t pb = n_bid > 0 ? bk.template best_px<0>() : -1;
+                        const int64_t pa = n_ask > 0 ? bk.template best_px<1>() : -1;
+                        int32_t px[4];
+                        px[0] = (int32_t)pb;  // far touch
+                        if (n_bid > 0 && n_ask > 0) {
+                            const int64_t two_t = 2 * (int64_t)a.tick;  // mid, up to the grid
+                            px[1] = (int32_t)((pb + pa + two_t - 1) / two_t * a.tick);
+                        } else {
+                            px[1] = (int32_t)(n_bid > 0 ? pb : pa);
+                        }
+                        px[2] = (int32_t)pa;  // near touch
+                        const int64_t pp = pa + (int64_t)a.passive_ticks * a.tick;
+                        px[3] = (n_ask > 0 && pp <= kMaxInt) ? (int32_t)pp : -1;
+                        int64_t remaining = (int64_t)a.parent - es.submitted;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const double x = (double)av[k];
+                            int64_t q = 0;
+                            if (x >= 1.0 && remaining > 0) {
+                                const double w = floor(x);
+                                q = w >= (double)remaining ? remaining : (int64_t)w;
+                            }
+                            if (px[k] <= 0 || q <= 0) continue;
+                            stage(OP_LIMIT_ASK, px[k], (int32_t)q);
+                            remaining -= q;
+                        }
+                    } else if (t < a.n_steps - 1) {
                         if (n_ask > 0) es.last_ask = bk.template best_px<1>();
                         const int64_t remaining = (int64_t)a.parent - es.submitted;
                         const int64_t steps_left = (int64_t)a.n_steps - t;
@@ -378,6 +411,53 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
     }
 }
 
+// Observation vector (Sec. 5.2.2) from one step's level-1 trace and the
+// environment state; one thread per (environment, message), grid-stride.
+__global__ void k_env_observe(const EnvStateDev* __restrict__ env, const Msg* __restrict__ replay,
+                              int64_t stride_env, const int4* __restrict__ l1, int32_t M,
+                              int32_t n_envs, int64_t passive_off, int32_t parent,
+                              float* __restrict__ obs)
+{
+    const int64_t row = 6 * (int64_t)M + 8;
+    const int64_t total = (int64_t)n_envs * M;
+    const int64_t kSec = 1000000000;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / M;
+        const int32_t k = (int32_t)(i - b * M);
+        const int4 r = l1[i];  // best bid price, its qty, best ask price, its qty
+        const bool hb = r.x > 0, ha = r.z > 0;
+        double mid = -1.0;
+        if (hb && ha)
+            mid = __ddiv_rn(__dadd_rn((double)r.x, (double)r.z), 2.0);
+        else if (hb)
+            mid = (double)r.x;
+        else if (ha)
+            mid = (double)r.z;
+        float* o = obs + b * row;
+        o[k] = __int2float_rn(r.x);
+        o[M + k] = __int2float_rn(r.z);
+        o[2 * M + k] = __double2float_rn(mid);
+        o[3 * M + k] = __ll2float_rn(ha ? (int64_t)r.z + passive_off : -1);
+        o[4 * M + k] = __ll2float_rn(hb && ha ? (int64_t)r.z - r.x : -1);
+        o[5 * M + 8 + k] = __ll2float_rn((int64_t)r.w - r.y);
+        if (k == M - 1) {
+            const EnvStateDev es = env[b];
+            const int64_t t_init = replay[b * stride_env].time_ns;
+            const int64_t tc = es.last_time, te = es.last_time - t_init;
+            float* sc = o + 5 * M;
+            sc[0] = __ll2float_rn(tc / kSec);
+            sc[1] = __ll2float_rn(tc % kSec);
+            sc[2] = __ll2float_rn(te / kSec);
+            sc[3] = __ll2float_rn(te % kSec);
+            sc[4] = __double2float_rn(es.p_init);
+            sc[5] = __double2float_rn(mid >= 0.0 ? __dsub_rn(mid, es.p_init) : 0.0);
+            sc[6] = __int2float_rn(parent);
+            sc[7] = __ll2float_rn(es.executed);
+        }
+    }
+}
+
 const void* env_kernel(int K, bool trace)
 {
 #define LOB_ENV_K(k)                                                                   \
@@ -441,7 +521,7 @@ int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, vo
 {
     if (!out || !book || !cfg || cfg->n_steps < 1 || cfg->parent_qty < 0 || cfg->depth < 1 ||
         cfg->depth > 64 || cfg->msgs_per_step < 1 || cfg->msgs_per_step > 1024 ||
-        cfg->p_init_fallback < 1) {
+        cfg->p_init_fallback < 1 || cfg->passive_ticks < 0 || cfg->tick_size < 1) {
         lob_set_error("lob_env_create: invalid argument");
         return LOB_E_INVAL;
     }
@@ -522,12 +602,14 @@ int lob_env_reset(lob_env* e, void* stream)
 }
 
 int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32_t step0,
-                int32_t n_run, const uint32_t* d_draws, float* d_reward, int32_t* d_bid_px,
-                int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty, int64_t* d_fills,
-                int32_t* d_l1, void* stream)
+                int32_t n_run, const uint32_t* d_draws, const float* d_actions, float* d_reward,
+                int32_t* d_bid_px, int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty,
+                int64_t* d_fills, int32_t* d_l1, void* stream)
 {
-    if (!e || !d_replay || !d_draws || !d_reward || !d_bid_px || !d_bid_qty || !d_ask_px ||
-        !d_ask_qty || !d_fills || n_run < 1 || step0 < 0 || step0 + n_run > e->cfg.n_steps ||
+    // exactly one agent source: the stand-in's draws or the policy's actions
+    if (!e || !d_replay || (!d_draws == !d_actions) || !d_reward || !d_bid_px || !d_bid_qty ||
+        !d_ask_px || !d_ask_qty || !d_fills || n_run < 1 || step0 < 0 ||
+        step0 + n_run > e->cfg.n_steps ||
         stride_env < (int64_t)e->cfg.n_steps * e->cfg.msgs_per_step) {
         lob_set_error("lob_env_run: invalid argument (step0=%d n_run=%d)", step0, n_run);
         return LOB_E_INVAL;
@@ -573,6 +655,9 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     a.wait_ns = kEnvWaitNs;
     a.l1 = d_l1;
     a.snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) ? 1 : 0;
+    a.actions = d_actions;
+    a.passive_ticks = e->cfg.passive_ticks;
+    a.tick = e->cfg.tick_size;
     const int W = e->warps;
     int grid = (a.n_envs + W - 1) / W;
     const int resident = c->num_sms * e->per_sm;
@@ -584,6 +669,33 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     if (err != cudaSuccess) return lob_cuda_fail(err, "lob_env_run launch");
     c->launches += 1;
     e->launches += 1;
+    return LOB_OK;
+}
+
+int lob_env_observe(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env,
+                    const int32_t* d_l1, float* d_obs, void* stream)
+{
+    if (!e || !d_replay || !d_l1 || !d_obs ||
+        stride_env < (int64_t)e->cfg.n_steps * e->cfg.msgs_per_step) {
+        lob_set_error("lob_env_observe: invalid argument");
+        return LOB_E_INVAL;
+    }
+    if (((uintptr_t)d_l1 & 15u) != 0 || ((uintptr_t)d_replay & 7u) != 0) {
+        lob_set_error("lob_env_observe: trace must be 16-byte and messages 8-byte aligned");
+        return LOB_E_INVAL;
+    }
+    lob_ctx* c = e->book;
+    const int M = e->cfg.msgs_per_step;
+    const int64_t total = (int64_t)c->cfg.n_books * M;
+    const int64_t need = (total + 255) / 256;
+    const int grid = (int)(need < (int64_t)c->num_sms * 8 ? need : (int64_t)c->num_sms * 8);
+    k_env_observe<<<grid, 256, 0, (cudaStream_t)stream>>>(
+        e->d_state, reinterpret_cast<const Msg*>(d_replay), stride_env,
+        reinterpret_cast<const int4*>(d_l1), M, c->cfg.n_books,
+        (int64_t)e->cfg.passive_ticks * e->cfg.tick_size, e->cfg.parent_qty, d_obs);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return lob_cuda_fail(err, "lob_env_observe launch");
+    c->launches += 1;
     return LOB_OK;
 }
 

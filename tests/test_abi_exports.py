@@ -47,7 +47,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_cpu_only_calls_fail_cleanly(lib):
     lib.lob_abi_version.restype = ctypes.c_int
-    assert lib.lob_abi_version() == 1
+    assert lib.lob_abi_version() == 2
     lib.lob_destroy.argtypes = [ctypes.c_void_p]
     assert lib.lob_destroy(None) == 0
     lib.lob_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]

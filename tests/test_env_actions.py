@@ -134,3 +134,140 @@ def test_observation_missing_sides():
     np.testing.assert_array_equal(obs[4 * M:5 * M], [-1, -1, -1])       # spread needs both
     np.testing.assert_array_equal(obs[5 * M:5 * M + 8], [34200, 5, 0, 5, 10_000, 0, 10, 0])
     np.testing.assert_array_equal(obs[5 * M + 8:], [-5, 4, 0])
+
+
+# ----------------------------------------------------------------------------- GPU parity
+
+AGENT = 1_000_000
+
+
+def _random_actions(rng, n_steps, n_env):
+    """Sizes of every kind the map must handle: whole and fractional, below
+    one share, negative, zero, NaN, +-inf, and larger than the task."""
+    a = rng.uniform(0.0, 40.0, (n_steps, n_env, 4)).astype(np.float32)
+    pick = rng.random((n_steps, n_env, 4))
+    a[pick < 0.15] = 0.0
+    a[(pick >= 0.15) & (pick < 0.2)] = 0.5
+    a[(pick >= 0.2) & (pick < 0.23)] = -3.0
+    a[(pick >= 0.23) & (pick < 0.25)] = np.nan
+    a[(pick >= 0.25) & (pick < 0.26)] = np.inf
+    a[(pick >= 0.26) & (pick < 0.27)] = -np.inf
+    a[(pick >= 0.27) & (pick < 0.29)] = 1e9
+    a[(pick >= 0.29) & (pick < 0.35)] = np.floor(a[(pick >= 0.29) & (pick < 0.35)])
+    return a
+
+
+def _oracle_episode(m, n_env, n_steps, per, actions, cap, tcap, parent, ticks, tick):
+    env = oracle.EnvOracle(n_env, cap, tcap, n_steps=n_steps, parent_qty=parent, agent_tid=AGENT,
+                           depth=10, passive_ticks=ticks, tick_size=tick)
+    rows = m.reshape(n_env, n_steps, per)
+    t_init = rows[:, 0, 0]["time_ns"].astype(np.int64)
+    off = np.arange(0, n_env * per + 1, per, dtype=np.int64)
+    outs, obs = [], []
+    for t in range(n_steps):
+        step = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
+        reward, lv, fills, tr = env.step(step, off, None, t, l1=True, actions=actions[t])
+        outs.append((reward, lv, fills, tr.reshape(n_env, per, 4), env.state()[0]))
+        obs.append(env.observe(tr, per, t_init))
+    return env, outs, obs
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cap,per,ticks,tick", [(7, 40, 2, 1), (100, 100, 3, 1), (250, 64, 1, 5)])
+def test_gpu_action_steps_and_observations_match_oracle(cap, per, ticks, tick):
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    from engine_harness import assert_same, gpu_outputs, oracle_outputs
+    n_env, n_steps, parent, tcap = 48, 9, 700, 2048
+    p = lobgen.make_params(777 + cap)
+    m, _ = lobgen.generate(p, [n_steps * per] * n_env)
+    if tick > 1:  # the coarse-tick case: every price on the tick grid
+        lim = m["type"] != 4
+        m["price"] = np.where(lim, m["price"] * tick, m["price"])
+    rng = np.random.default_rng(cap)
+    actions = _random_actions(rng, n_steps, n_env)
+    oenv, oouts, oobs = _oracle_episode(m, n_env, n_steps, per, actions, cap, tcap, parent,
+                                        ticks, tick)
+
+    e = eng.Engine(n_env, cap, tcap)
+    env = eng.Env(e, n_steps=n_steps, parent_qty=parent, agent_tid=AGENT, depth=10,
+                  msgs_per_step=per, passive_ticks=ticks, tick_size=tick)
+    d = eng.messages_to_device(m)
+    act = torch.from_numpy(actions).cuda()
+    out = env.outputs(n_steps)
+    l1 = torch.empty((n_steps, n_env, per, 4), dtype=torch.int32, device="cuda")
+    stride = n_steps * per
+    for t in range(n_steps):  # one step per launch, the observation after each
+        env.run(d, stride, t, 1, None, out, row0=t, l1=l1[t:t + 1], actions=act[t:t + 1])
+        ob = env.observe(d, stride, l1[t]).cpu().numpy()
+        assert ob.tobytes() == oobs[t].tobytes(), "observation differs at step %d: %s" % (
+            t, np.argwhere(ob != oobs[t])[:4])
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    gl1 = l1.cpu().numpy()
+    for t in range(n_steps):
+        reward, lv, fills, tr, _ = oouts[t]
+        assert g["reward"][t].tobytes() == reward.tobytes(), t
+        assert np.array_equal(g["fills"][t], fills), t
+        for name, v in zip(("bid_px", "bid_qty", "ask_px", "ask_qty"), lv):
+            assert np.array_equal(g[name][t], v), (name, t)
+        assert np.array_equal(gl1[t], tr), t
+    st, p0 = env.state()
+    ost, op0 = oenv.state()
+    assert np.array_equal(st.cpu().numpy(), ost)
+    assert p0.cpu().numpy().tobytes() == op0.tobytes()
+    assert_same(gpu_outputs(e), oracle_outputs(oenv.books))
+    # the cap was exercised: some tasks were fully placed before the last step
+    assert (oouts[n_steps - 2][4][:, 0] == parent).any()
+    env.close()
+    e.close()
+
+
+@pytest.mark.gpu
+def test_gpu_action_episode_in_one_launch_matches_per_step():
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    n_env, n_steps, per, cap, parent = 64, 12, 50, 100, 400
+    m, _ = lobgen.generate(lobgen.make_params(31337), [n_steps * per] * n_env)
+    actions = _random_actions(np.random.default_rng(5), n_steps, n_env)
+    act = torch.from_numpy(actions).cuda()
+    d = eng.messages_to_device(m)
+    res = []
+    for splits in ([1] * n_steps, [n_steps], [5, 7]):
+        e = eng.Engine(n_env, cap, 1024)
+        env = eng.Env(e, n_steps=n_steps, parent_qty=parent, agent_tid=AGENT, msgs_per_step=per)
+        out = env.outputs(n_steps)
+        t = 0
+        for k in splits:
+            env.run(d, n_steps * per, t, k, None, out, row0=t, actions=act[t:t + k])
+            t += k
+        torch.cuda.synchronize()
+        st, _ = env.state()
+        res.append(({k: v.cpu().numpy() for k, v in out.items()}, st.cpu().numpy()))
+        env.close()
+        e.close()
+    for r in res[1:]:
+        for k in r[0]:
+            assert r[0][k].tobytes() == res[0][0][k].tobytes(), k
+        assert np.array_equal(r[1], res[0][1])
+
+
+@pytest.mark.gpu
+def test_gpu_env_run_needs_exactly_one_agent_source():
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    e = eng.Engine(4, 16, 64)
+    env = eng.Env(e, n_steps=3, msgs_per_step=8)
+    d = torch.zeros((4 * 24, 32), dtype=torch.uint8, device="cuda")
+    out = env.outputs(1)
+    dr = torch.zeros((1, 4), dtype=torch.int32, device="cuda")
+    act = torch.zeros((1, 4, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(eng.LobError):
+        env.run(d, 24, 0, 1, None, out)
+    with pytest.raises(eng.LobError):
+        env.run(d, 24, 0, 1, dr, out, actions=act)
+    env.close()
+    e.close()
