@@ -501,11 +501,48 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
     forms["graph_per_step"] = float(np.mean(times))
     res["graph_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snapshot()))
     del g
+    std_out = {k: v.cpu().numpy() for k, v in out.items()}  # the stand-in agent's episode
+    # policy loop (Sec. 5.2.2-5.2.3): every step acts on four sizes and ends
+    # with the step's level-1 trace and the observation vector, as a policy in
+    # the loop needs; the sizes are seeded stand-ins for a policy's output
+    gen_a = torch.Generator(device="cuda")
+    gen_a.manual_seed(w["seed"] + 2)
+    act = torch.rand((steps, n, 4), generator=gen_a, device="cuda") * 4.0
+    l1 = torch.empty((1, n, per, 4), dtype=torch.int32, device="cuda")
+    obs = torch.empty((n, 6 * per + 8), dtype=torch.float32, device="cuda")
+
+    def policy_steps():
+        e.reset()
+        env.reset()
+        for t in range(steps):
+            env.run(dm, stride, t, 1, None, out, row0=t, l1=l1, actions=act[t:t + 1])
+            env.observe(dm, stride, l1[0], obs)
+
+    s3 = torch.cuda.Stream()
+    s3.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s3):
+        with torch.cuda.graph(g, stream=s3):
+            policy_steps()
+    torch.cuda.current_stream().wait_stream(s3)
+    for name, fn in (("policy_per_step", policy_steps), ("policy_graph", g.replay)):
+        times = []
+        for i in range(max(1, args.warmup) + max(2, args.steps // 3)):
+            a, b = _events()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if i >= max(1, args.warmup):
+                times.append(a.elapsed_time(b))
+        forms[name] = float(np.mean(times))
+    del g
     for name, ms in forms.items():
         res[name] = {"ms_per_episode": round(ms, 3),
                      "env_steps_per_s": round(n * steps / ms * 1e3, 1),
                      "data_msgs_per_s": round(n * steps * per / ms * 1e3, 1),
-                     "launches": 1 if name == "persistent_episode" else steps}
+                     "launches": (1 if name == "persistent_episode" else
+                                  2 * steps if name.startswith("policy") else steps)}
     if rank == 0:
         sample = np.array([0, 1, 2, n // 2, n - 1])
         hm, hoff = lobgen.generate(params, [steps * per] * len(sample), stream_ids=ids[sample])
@@ -513,9 +550,7 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
         oenv = oracle.EnvOracle(len(sample), w["capacity"], 4096, n_steps=steps)
         rows = hm.reshape(len(sample), steps, per)
         ok = True
-        rew = out["reward"].cpu().numpy()
-        fills = out["fills"].cpu().numpy()
-        lvb = out["bid_px"].cpu().numpy()
+        rew, fills, lvb = std_out["reward"], std_out["fills"], std_out["bid_px"]
         for t in range(steps):
             stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
             r_, lv, f_ = oenv.step(stp, np.arange(0, len(sample) * per + 1, per), hd[t], t)
@@ -524,6 +559,25 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
             ok &= np.array_equal(lvb[t, sample], lv[0])
         res["parity"] = {"envs_checked": int(len(sample)), "steps_checked": steps,
                          "bit_exact": bool(ok)}
+        # the policy form's last run (still in `out`): rewards, fills, best
+        # bids per step and the final observation
+        oenv = oracle.EnvOracle(len(sample), w["capacity"], 4096, n_steps=steps)
+        ha = act.cpu().numpy()[:, sample]
+        t_init = rows[:, 0, 0]["time_ns"].astype(np.int64)
+        rew = out["reward"].cpu().numpy()
+        fills = out["fills"].cpu().numpy()
+        lvb = out["bid_px"].cpu().numpy()
+        ok = True
+        for t in range(steps):
+            stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
+            r_, lv, f_, tr = oenv.step(stp, np.arange(0, len(sample) * per + 1, per), None, t,
+                                       l1=True, actions=ha[t])
+            ok &= rew[t, sample].tobytes() == r_.tobytes()
+            ok &= np.array_equal(fills[t, sample], f_)
+            ok &= np.array_equal(lvb[t, sample], lv[0])
+        ok_obs = oenv.observe(tr, per, t_init).tobytes() == obs.cpu().numpy()[sample].tobytes()
+        res["policy_parity"] = {"envs_checked": int(len(sample)), "steps_checked": steps,
+                                "bit_exact": bool(ok), "final_observation_bit_exact": bool(ok_obs)}
     env.close()
     e.close()
     del dm, out

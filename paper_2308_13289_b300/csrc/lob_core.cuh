@@ -1295,24 +1295,59 @@ __device__ __forceinline__ void emit_levels(const int32_t (&px)[K], const int32_
     __syncwarp();
 }
 
-// Level-1 state of one side after a message (Sec. 5.2.1): best price and the
-// summed quantity of the orders at it (the level-0 prefix of the sorted side),
-// (-1, 0) when empty, quantity saturating at INT32_MAX.
-template <int K, int X, class Book>
-__device__ __forceinline__ int2 level1_side(Book& bk, int n)
+// Level-1 state of both sides (Sec. 5.2.1): the best price and the summed
+// quantity of the orders at it (the level-0 prefix of each sorted side),
+// (-1, 0) for an empty side, quantity saturating at INT32_MAX.  The result is
+// valid in lane 0 (the lane that stores it).
+template <int K>
+__device__ __forceinline__ void level1_scan(const char* side, int n, int32_t& p, int64_t& q)
 {
-    if (n == 0) return make_int2(-1, 0);
-    const int l = lane_id();
-    SideVec<K> tmp;
-    SideVec<K>& v = bk.template acquire<X>(tmp);
-    const int32_t best = __shfl_sync(kFull, v.px[0], 0);
-    int64_t loc = 0;
+    const int32_t* px = reinterpret_cast<const int32_t*>(side + Geo<K>::PX);
+    const int32_t* qt = reinterpret_cast<const int32_t*>(side + Geo<K>::QTY);
+    p = px[0];
+    q = 0;
+#pragma unroll 1
+    for (int i = 0; i < n && px[i] == p; ++i) q += qt[i];
+}
+
+template <int K, class Book>
+__device__ __forceinline__ int4 level1_book(Book& bk, int n_bid, int n_ask)
+{
+    int32_t pb = -1, pa = -1;
+    int64_t qb = 0, qa = 0;
+    if constexpr (!Book::kInRegisters) {
+        // shared memory: lane 0 walks the best level of each side (a few orders)
+        if (lane_id() == 0) {
+            if (n_bid > 0) level1_scan<K>(bk.template side<0>(), n_bid, pb, qb);
+            if (n_ask > 0) level1_scan<K>(bk.template side<1>(), n_ask, pa, qa);
+        }
+    } else {
+        // registers: every lane sums its slots at the best price, then one warp
+        // reduction per side (32-bit while no lane's part can overflow it)
+        const int l = lane_id();
+        SideVec<K> tmp;
+        SideVec<K>& vb = bk.template acquire<0>(tmp);
+        SideVec<K>& va = bk.template acquire<1>(tmp);
+        const int32_t bb = __shfl_sync(kFull, vb.px[0], 0);
+        const int32_t ba = __shfl_sync(kFull, va.px[0], 0);
+        int64_t lb = 0, la = 0;
 #pragma unroll
-    for (int j = 0; j < K; ++j) loc += (l * K + j < n && v.px[j] == best) ? v.q[j] : 0;
-    // the level ends inside lane 0 unless lane 0's last slot is still at the best price
-    const bool spans = __shfl_sync(kFull, (int)(K < n && v.px[K - 1] == best), 0) != 0;
-    const int64_t vol = spans ? warp_sum64(loc) : __shfl_sync(kFull, loc, 0);
-    return make_int2(best, (int32_t)min(vol, (int64_t)kMaxInt));
+        for (int j = 0; j < K; ++j) {
+            lb += (l * K + j < n_bid && vb.px[j] == bb) ? vb.q[j] : 0;
+            la += (l * K + j < n_ask && va.px[j] == ba) ? va.q[j] : 0;
+        }
+        if (!__any_sync(kFull, ((lb | la) >> 27) != 0)) {  // 32 parts < 2^27: no overflow
+            qb = __reduce_add_sync(kFull, (unsigned)lb);
+            qa = __reduce_add_sync(kFull, (unsigned)la);
+        } else {
+            qb = warp_sum64(lb);
+            qa = warp_sum64(la);
+        }
+        pb = n_bid > 0 ? bb : -1;
+        pa = n_ask > 0 ? ba : -1;
+    }
+    return make_int4(pb, (int32_t)min(qb, (int64_t)kMaxInt), pa,
+                     (int32_t)min(qa, (int64_t)kMaxInt));
 }
 
 }  // namespace lob

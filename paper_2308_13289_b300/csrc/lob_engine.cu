@@ -215,11 +215,8 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                 apply_message<K, false>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
                                  hb.z, hb.w, ts, tally, obs, a.snap != 0);
                 if constexpr (kTrace) {
-                    const int2 lb = level1_side<K, 0>(bk, n_bid);
-                    const int2 la = level1_side<K, 1>(bk, n_ask);
-                    if (l == 0)
-                        reinterpret_cast<int4*>(a.l1)[lo + (int64_t)c * chunk + i] =
-                            make_int4(lb.x, lb.y, la.x, la.y);
+                    const int4 top = level1_book<K>(bk, n_bid, n_ask);
+                    if (l == 0) reinterpret_cast<int4*>(a.l1)[lo + (int64_t)c * chunk + i] = top;
                 }
             }
             __syncwarp();

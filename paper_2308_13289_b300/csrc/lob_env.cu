@@ -310,12 +310,10 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                     apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
                                      hb.y, hb.z, hb.w, ts, tally, obs, a.snap != 0);
                     if (kTrace && phase == 0) {
-                        const int2 lb = level1_side<K, 0>(bk, n_bid);
-                        const int2 la = level1_side<K, 1>(bk, n_ask);
+                        const int4 top = level1_book<K>(bk, n_bid, n_ask);
                         if (l == 0)
                             reinterpret_cast<int4*>(a.l1)[((int64_t)r * a.n_envs + b) *
-                                                              a.msgs_per_step + i] =
-                                make_int4(lb.x, lb.y, la.x, la.y);
+                                                              a.msgs_per_step + i] = top;
                     }
                 }
             }
@@ -412,20 +410,19 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
 }
 
 // Observation vector (Sec. 5.2.2) from one step's level-1 trace and the
-// environment state; one thread per (environment, message), grid-stride.
+// environment state: one CTA per environment (grid-stride over environments),
+// thread k handles message k of the step.
 __global__ void k_env_observe(const EnvStateDev* __restrict__ env, const Msg* __restrict__ replay,
                               int64_t stride_env, const int4* __restrict__ l1, int32_t M,
                               int32_t n_envs, int64_t passive_off, int32_t parent,
                               float* __restrict__ obs)
 {
     const int64_t row = 6 * (int64_t)M + 8;
-    const int64_t total = (int64_t)n_envs * M;
     const int64_t kSec = 1000000000;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = i / M;
-        const int32_t k = (int32_t)(i - b * M);
-        const int4 r = l1[i];  // best bid price, its qty, best ask price, its qty
+    const int k = threadIdx.x;
+    for (int b = blockIdx.x; b < n_envs; b += gridDim.x) {
+        if (k >= M) continue;
+        const int4 r = l1[(int64_t)b * M + k];  // best bid price, its qty, best ask price, its qty
         const bool hb = r.x > 0, ha = r.z > 0;
         double mid = -1.0;
         if (hb && ha)
@@ -434,7 +431,7 @@ __global__ void k_env_observe(const EnvStateDev* __restrict__ env, const Msg* __
             mid = (double)r.x;
         else if (ha)
             mid = (double)r.z;
-        float* o = obs + b * row;
+        float* o = obs + (int64_t)b * row;
         o[k] = __int2float_rn(r.x);
         o[M + k] = __int2float_rn(r.z);
         o[2 * M + k] = __double2float_rn(mid);
@@ -443,7 +440,7 @@ __global__ void k_env_observe(const EnvStateDev* __restrict__ env, const Msg* __
         o[5 * M + 8 + k] = __ll2float_rn((int64_t)r.w - r.y);
         if (k == M - 1) {
             const EnvStateDev es = env[b];
-            const int64_t t_init = replay[b * stride_env].time_ns;
+            const int64_t t_init = replay[(int64_t)b * stride_env].time_ns;
             const int64_t tc = es.last_time, te = es.last_time - t_init;
             float* sc = o + 5 * M;
             sc[0] = __ll2float_rn(tc / kSec);
@@ -686,10 +683,9 @@ int lob_env_observe(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env,
     }
     lob_ctx* c = e->book;
     const int M = e->cfg.msgs_per_step;
-    const int64_t total = (int64_t)c->cfg.n_books * M;
-    const int64_t need = (total + 255) / 256;
-    const int grid = (int)(need < (int64_t)c->num_sms * 8 ? need : (int64_t)c->num_sms * 8);
-    k_env_observe<<<grid, 256, 0, (cudaStream_t)stream>>>(
+    const int threads = (M + 31) / 32 * 32;  // msgs_per_step <= 1024
+    const int grid = c->cfg.n_books < c->num_sms * 16 ? c->cfg.n_books : c->num_sms * 16;
+    k_env_observe<<<grid, threads, 0, (cudaStream_t)stream>>>(
         e->d_state, reinterpret_cast<const Msg*>(d_replay), stride_env,
         reinterpret_cast<const int4*>(d_l1), M, c->cfg.n_books,
         (int64_t)e->cfg.passive_ticks * e->cfg.tick_size, e->cfg.parent_qty, d_obs);
