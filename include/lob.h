@@ -337,6 +337,31 @@ int lob_env_observe(lob_env* env, const lob_msg_t* d_replay, int64_t stride_env,
  * last data time; double[n_books] = P_init.  Either pointer may be NULL. */
 int lob_env_get_state(lob_env* env, int64_t* d_state, double* d_p_init, void* stream);
 
+/* ------------------------------------------------- paper-literal ablation */
+
+/* The paper's own formulation of the book (Sec. 4, eqs. 1-2; Sec. 4.1), kept
+ * as an ablation of this library's sorted-side design: each side an UNSORTED
+ * array of `capacity` slots with -1 marking an empty slot; add writes an empty
+ * slot, cancel finds the OID by a full scan, matching takes Best(o) by a full
+ * arg-max / arg-min (earliest arrival among equal prices) once per fill, and
+ * every slot with Q <= 0 is reset to -1 after every fill and operation.  With
+ * all_branches = 1 every message also runs all three branches of the dispatch
+ * (limit, cancel/delete, market), each on its own copy of the book, and keeps
+ * its own one -- what `vmap` does with a branch (Sec. 4.3).
+ * Every book starts EMPTY and runs d_msgs[d_offsets[b] .. d_offsets[b+1]);
+ * the results equal lob_process_batch's on the same input (same full-side
+ * rule, no snapshot rule): d_trades lob_trade_t[n_books][trade_capacity]
+ * (-1 past the stored ones), d_trade_counts int64[n_books], and the final
+ * books in lob_get_book's canonical layout ([n_books][2][capacity], priority
+ * order, -1 padded; d_count int32[n_books][2]).  No counters.  capacity
+ * 1..128; d_msgs 16-byte aligned; nothing is allocated.  LOB_E_INVAL on a bad
+ * argument. */
+int lob_literal_process(const lob_msg_t* d_msgs, const int64_t* d_offsets, int32_t n_books,
+                        int32_t capacity, int32_t trade_capacity, int32_t overflow_rule,
+                        int32_t all_branches, lob_trade_t* d_trades, int64_t* d_trade_counts,
+                        int32_t* d_price, int32_t* d_qty, int32_t* d_oid, int32_t* d_tid,
+                        int64_t* d_time, int32_t* d_count, void* stream);
+
 /* ------------------------------------------------------ allocation-free call */
 
 /* No counterpart in the paper: an engineering addition for callers that must

@@ -195,6 +195,35 @@ def lob_env_get_state(e, state, p_init, stream=None):
           "lob_env_get_state")
 
 
+def lob_literal_process(msgs, offsets, n_books, capacity, trade_capacity, overflow_rule,
+                        all_branches, trades, trade_counts, px, qty, oid, tid, tm, count,
+                        stream=None):
+    check(lib().lob_literal_process(_ptr(msgs), _ptr(offsets), n_books, capacity,
+                                    trade_capacity, overflow_rule, int(all_branches),
+                                    _ptr(trades), _ptr(trade_counts), _ptr(px), _ptr(qty),
+                                    _ptr(oid), _ptr(tid), _ptr(tm), _ptr(count),
+                                    _stream(stream)), "lob_literal_process")
+
+
+def literal_process(msgs, offsets, capacity, trade_capacity, overflow_rule=OVERFLOW_EVICT,
+                    all_branches=True, stream=None):
+    """The paper-literal ablation (lob_literal_process): every book from empty
+    over its segment.  Returns (book dict in the Engine.book() layout, trades
+    [n, trade_capacity, 8] int32 view, trade counts)."""
+    n = offsets.numel() - 1
+    shape = (n, 2, capacity)
+    bk = {k: torch.empty(shape, dtype=torch.int32, device="cuda")
+          for k in ("price", "qty", "oid", "tid")}
+    bk["time_ns"] = torch.empty(shape, dtype=torch.int64, device="cuda")
+    bk["count"] = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+    tr = torch.empty((n, max(1, trade_capacity), 8), dtype=torch.int32, device="cuda")
+    cnt = torch.empty(n, dtype=torch.int64, device="cuda")
+    lob_literal_process(msgs, offsets, n, capacity, trade_capacity, overflow_rule, all_branches,
+                        tr, cnt, bk["price"], bk["qty"], bk["oid"], bk["tid"], bk["time_ns"],
+                        bk["count"], stream)
+    return bk, tr[:, :trade_capacity], cnt
+
+
 # ------------------------------------------------------------------ convenience object
 
 def snapshot_books(bid_px, bid_qty, ask_px, ask_qty, capacity, time_ns=0):
