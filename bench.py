@@ -342,7 +342,8 @@ def run_engine(args):
         torch.cuda.empty_cache()
         extras = {"uneven_4096_lognormal": run_uneven(args, rank),
                   "rl_exec_8192x400": run_rl(args, rank),
-                  "serving_mix": run_serving(args, rank)}
+                  "serving_mix": run_serving(args, rank),
+                  "ablation_paper_literal": run_ablation(args, rank)}
         e = eng.Engine(1, cap, 1)
 
     if rank == 0:
@@ -371,6 +372,67 @@ def run_engine(args):
 def _events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_ablation(args, rank, name="replay_1024x10k"):
+    """The design ablation on 1,024 books x 10^4 messages: this library's
+    sorted warp sides (one persistent launch) against the paper's own
+    formulation on the GPU -- unsorted arrays with full scans, branching on
+    the message type, and with every branch run on a copy of the book (what
+    vmap does) -- all bit-exact with one another."""
+    import torch
+
+    import lobgen
+    import paper_2308_13289_b300 as eng
+    w = lobgen.WORKLOADS[name]
+    n, per, cap = w["n_books"], w["msgs"], w["capacity"]
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    ids = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
+    gen = lobgen.DeviceStreams(params, n, stream_ids=ids)
+    dm, doff = gen.advance([per] * n)
+    del gen
+    tcap = per
+    total = n * per
+
+    def timed(fn, reps):
+        times = []
+        for i in range(1 + reps):
+            a, b = _events()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            if i >= 1:
+                times.append(a.elapsed_time(b))
+        return float(np.mean(times))
+
+    e = eng.Engine(n, cap, tcap)
+
+    def sorted_form():
+        e.reset()
+        e.process_batch(dm, doff)
+
+    res = {"workload": name, "n_books": n, "messages": total, "capacity": cap}
+    ms = timed(sorted_form, max(3, args.steps))
+    res["sorted_warp_sides"] = {"ms_per_step": round(ms, 4), "msgs_per_s": round(total / ms * 1e3, 1)}
+    ref = {k: v.clone() for k, v in e.book().items()}
+    _, ref_cnt = e.trades()
+    e.close()
+    for form, allb in (("literal_branching", False), ("literal_all_branches", True)):
+        out = {}
+
+        def lit():
+            out["r"] = eng.literal_process(dm, doff, cap, tcap, eng.OVERFLOW_EVICT, allb)
+
+        ms_l = timed(lit, 2)
+        bk, _, cnt = out["r"]
+        same = all(torch.equal(bk[k], ref[k]) for k in ref) and torch.equal(cnt, ref_cnt)
+        res[form] = {"ms_per_step": round(ms_l, 4), "msgs_per_s": round(total / ms_l * 1e3, 1),
+                     "slowdown_vs_sorted": round(ms_l / ms, 2), "bit_exact_vs_sorted": bool(same)}
+        del out
+    del dm, doff
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_uneven(args, rank):
@@ -758,6 +820,9 @@ def run_single(args):
     elif wl.startswith("uneven"):
         r = run_uneven(args, rank)
         value, unit = r["natural"]["msgs_per_s"], UNIT
+    elif wl == "ablation":
+        r = run_ablation(args, rank)
+        value, unit = r["sorted_warp_sides"]["msgs_per_s"], UNIT
     else:
         r = run_serving(args, rank)
         value, unit = r["steps_per_s"], "episode-steps/s"
@@ -772,7 +837,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload.startswith(("rl_exec", "uneven", "serving")):
+    elif args.workload.startswith(("rl_exec", "uneven", "serving", "ablation")):
         run_single(args)
     else:
         run_engine(args)
