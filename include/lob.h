@@ -204,6 +204,23 @@ int lob_inject_orders(lob_ctx* ctx, const lob_msg_t* d_msgs, const int64_t* d_of
 /* Restart every book's trade log (count 0). */
 int lob_clear_trades(lob_ctx* ctx, void* stream);
 
+/* Stream every book's messages from HOST memory through the engine, copy and
+ * compute overlapped (message replay, Sec. 4.3, fed from the host): book b's
+ * msgs_per_book messages sit at h_msgs[b*msgs_per_book ..] (book-major;
+ * page-locked memory, or the copies are not asynchronous).  Chunk k of every
+ * book (chunk_msgs messages, the last chunk shorter) is copied by one strided
+ * host-to-device copy on a stream of the context while chunk k-1 is being
+ * processed; the result equals one lob_process_batch over the same segments
+ * (books continue from their current state; the trade logs restart at the
+ * call unless LOB_FLAG_APPEND_TRADES).  The context allocates, on first use,
+ * three staging chunks of n_books*chunk_msgs*32 bytes (kept until
+ * lob_destroy; a larger chunk_msgs later reallocates them after a device
+ * synchronisation), a copy stream and events.  h_msgs must stay valid and
+ * unchanged until `stream` has passed the call.  Returns once all work is
+ * enqueued.  LOB_E_NOMEM when the staging does not fit. */
+int lob_process_host(lob_ctx* ctx, const lob_msg_t* h_msgs, int64_t msgs_per_book,
+                     int32_t chunk_msgs, void* stream);
+
 /* ----------------------------------------------------------------- outputs */
 
 /* Top `depth` price levels per side (Sec. 5.1.1 ten-level book state): for the

@@ -106,6 +106,19 @@ def lob_process_segments(h, msgs, starts, counts, book_ids, stream=None):
                                      book_ids.numel(), _stream(stream)), "lob_process_segments")
 
 
+def _host_ptr(t):
+    if t.is_cuda:
+        raise ValueError("expected a host tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lob_process_host(h, h_msgs, msgs_per_book, chunk_msgs, stream=None):
+    check(lib().lob_process_host(h, _host_ptr(h_msgs), int(msgs_per_book), int(chunk_msgs),
+                                 _stream(stream)), "lob_process_host")
+
+
 def lob_inject_orders(h, msgs, offsets, book_ids=None, n_active=None, stream=None):
     n = (offsets.numel() - 1) if n_active is None else n_active
     check(lib().lob_inject_orders(h, _ptr(msgs), _ptr(offsets), _ptr(book_ids), n,
@@ -291,6 +304,11 @@ class Engine:
 
     def process_batch(self, msgs, offsets, book_ids=None):
         lob_process_batch(self.h, msgs, offsets, book_ids, stream=self.stream)
+
+    def process_host(self, h_msgs, msgs_per_book, chunk_msgs=2000):
+        """Every book's messages from pinned host memory (book-major, equal
+        counts), copied chunk by chunk while the previous chunk is processed."""
+        lob_process_host(self.h, h_msgs, msgs_per_book, chunk_msgs, self.stream)
 
     def inject_orders(self, msgs, offsets, book_ids=None):
         lob_inject_orders(self.h, msgs, offsets, book_ids, stream=self.stream)

@@ -623,13 +623,20 @@ int lob_destroy(lob_ctx* c)
     if (!c) return LOB_OK;
     cudaError_t first = cudaSuccess;
     if (c->d_state || c->d_trades) first = cudaDeviceSynchronize();
+    if (c->copy_stream && first == cudaSuccess) first = cudaStreamSynchronize(c->copy_stream);
     void* ptrs[] = {c->d_state, c->d_counts, c->d_trades, c->d_tcounts,
-                    c->d_stats, c->d_status, c->d_queue};
+                    c->d_stats, c->d_status, c->d_queue, c->d_stage, c->d_stage_off};
     for (void* p : ptrs)
         if (p) {
             cudaError_t e = cudaFree(p);
             if (first == cudaSuccess) first = e;
         }
+    for (int i = 0; i < lob_ctx::kStages; ++i) {
+        if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+        if (c->ev_consumed[i]) cudaEventDestroy(c->ev_consumed[i]);
+    }
+    if (c->ev_start) cudaEventDestroy(c->ev_start);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     delete c;
     if (first != cudaSuccess) return lob_cuda_fail(first, "lob_destroy");
     return LOB_OK;
@@ -703,6 +710,111 @@ int lob_process_batch(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offs
     const int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
     return lob_launch_process(c, d_msgs, d_offsets, d_book_ids, n_active, append,
                               (cudaStream_t)stream, nullptr, nullptr);
+}
+
+namespace {
+
+// uniform offsets 0, L, 2L, ..., n*L
+__global__ void k_uniform_offsets(int64_t* off, int32_t n, int64_t len)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        off[i] = i * len;
+}
+
+// staging buffers, streams and events of the host-streamed ingest
+int setup_host_stream(lob_ctx* c, int64_t chunk)
+{
+    if (c->d_stage && c->stage_msgs >= chunk) return LOB_OK;
+    cudaError_t err = cudaSuccess;
+    if (c->d_stage) {
+        err = cudaStreamSynchronize(c->copy_stream);
+        if (err == cudaSuccess) err = cudaDeviceSynchronize();
+        if (err != cudaSuccess) return lob_cuda_fail(err, "lob_process_host");
+        cudaFree(c->d_stage);
+        c->d_stage = nullptr;
+    }
+    const size_t bytes = (size_t)lob_ctx::kStages * c->cfg.n_books * (size_t)chunk * 32;
+    err = cudaMalloc(&c->d_stage, bytes);
+    if (err != cudaSuccess) {
+        c->d_stage = nullptr;
+        lob_set_error("lob_process_host: staging (%zu bytes) does not fit on the device", bytes);
+        return LOB_E_NOMEM;
+    }
+    c->stage_msgs = chunk;
+    if (!c->d_stage_off) {
+        err = cudaMalloc(&c->d_stage_off, sizeof(int64_t) * 2 * ((size_t)c->cfg.n_books + 1));
+        if (err != cudaSuccess) {
+            c->d_stage_off = nullptr;
+            return lob_cuda_fail(err, "lob_process_host offsets");
+        }
+    }
+    if (!c->copy_stream) {
+        err = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+        for (int i = 0; i < lob_ctx::kStages && err == cudaSuccess; ++i) {
+            err = cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming);
+            if (err == cudaSuccess)
+                err = cudaEventCreateWithFlags(&c->ev_consumed[i], cudaEventDisableTiming);
+        }
+        if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->ev_start, cudaEventDisableTiming);
+        if (err != cudaSuccess) return lob_cuda_fail(err, "lob_process_host streams");
+    }
+    return LOB_OK;
+}
+
+}  // namespace
+
+int lob_process_host(lob_ctx* c, const lob_msg_t* h_msgs, int64_t msgs_per_book,
+                     int32_t chunk_msgs, void* stream)
+{
+    if (!c || (!h_msgs && msgs_per_book > 0) || msgs_per_book < 0 || chunk_msgs < 1) {
+        lob_set_error("lob_process_host: invalid argument");
+        return LOB_E_INVAL;
+    }
+    if (msgs_per_book == 0) return LOB_OK;
+    const int64_t chunk = chunk_msgs < msgs_per_book ? chunk_msgs : msgs_per_book;
+    int rc = setup_host_stream(c, chunk);
+    if (rc != LOB_OK) return rc;
+    const int n = c->cfg.n_books;
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n_chunks = (msgs_per_book + chunk - 1) / chunk;
+    const int64_t tail = msgs_per_book - (n_chunks - 1) * chunk;
+    // offsets of a full chunk and of the (possibly shorter) last chunk
+    int64_t* off_full = c->d_stage_off;
+    int64_t* off_tail = c->d_stage_off + (n + 1);
+    const int blocks = (n + 256) / 256;
+    k_uniform_offsets<<<blocks, 256, 0, s>>>(off_full, n, chunk);
+    k_uniform_offsets<<<blocks, 256, 0, s>>>(off_tail, n, tail);
+    cudaError_t err = cudaGetLastError();
+    // the copy stream starts after everything already queued on `stream`
+    if (err == cudaSuccess) err = cudaEventRecord(c->ev_start, s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(c->copy_stream, c->ev_start, 0);
+    if (err != cudaSuccess) return lob_cuda_fail(err, "lob_process_host");
+    const size_t slot_bytes = (size_t)n * (size_t)c->stage_msgs * 32;
+    int append = (c->cfg.flags & LOB_FLAG_APPEND_TRADES) ? 1 : 0;
+    for (int64_t k = 0; k < n_chunks; ++k) {
+        const int st = (int)(k % lob_ctx::kStages);
+        const int64_t len = k + 1 < n_chunks ? chunk : tail;
+        char* slot = c->d_stage + st * slot_bytes;
+        // chunk k of every book: a strided copy (row b = book b's messages
+        // [k*chunk, k*chunk + len)), into the slot in book-major order
+        if (k >= lob_ctx::kStages) err = cudaStreamWaitEvent(c->copy_stream, c->ev_consumed[st], 0);
+        if (err == cudaSuccess)
+            err = cudaMemcpy2DAsync(slot, (size_t)len * 32, h_msgs + k * chunk,
+                                    (size_t)msgs_per_book * 32, (size_t)len * 32, (size_t)n,
+                                    cudaMemcpyHostToDevice, c->copy_stream);
+        if (err == cudaSuccess) err = cudaEventRecord(c->ev_copied[st], c->copy_stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(s, c->ev_copied[st], 0);
+        if (err != cudaSuccess) return lob_cuda_fail(err, "lob_process_host copy");
+        rc = lob_launch_process(c, reinterpret_cast<const lob_msg_t*>(slot),
+                                k + 1 < n_chunks ? off_full : off_tail, nullptr, n, append, s,
+                                nullptr, nullptr);
+        if (rc != LOB_OK) return rc;
+        append = 1;  // later chunks continue the logs the first one began
+        err = cudaEventRecord(c->ev_consumed[st], s);
+        if (err != cudaSuccess) return lob_cuda_fail(err, "lob_process_host");
+    }
+    return LOB_OK;
 }
 
 int lob_process_batch_l1(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_offsets,

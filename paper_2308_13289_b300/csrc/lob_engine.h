@@ -25,6 +25,15 @@ struct lob_ctx {
     int ctas_per_sm_eff = 1;
     int smem_per_cta = 0;
     int64_t launches = 0;
+    // host-streamed ingest (lob_process_host), set up on first use
+    static constexpr int kStages = 3;
+    char* d_stage = nullptr;          // kStages x [n_books][stage_msgs] message slots
+    int64_t* d_stage_off = nullptr;   // uniform offsets 0, L, 2L, ... for every L <= stage_msgs
+    int64_t stage_msgs = 0;           // messages per book per staged chunk
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[kStages] = {};
+    cudaEvent_t ev_consumed[kStages] = {};
+    cudaEvent_t ev_start = nullptr;
 };
 
 void lob_set_error(const char* fmt, ...);

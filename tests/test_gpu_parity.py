@@ -228,3 +228,26 @@ def test_level1_trace_matches_oracle(eng, cap):
     assert np.array_equal(l1.cpu().numpy(), exp)
     # the traced run leaves the same books and trades as an untraced one
     assert_same(gpu_outputs(e), oracle_outputs(o))
+
+
+@pytest.mark.parametrize("chunk", [777, 5000, 12000])
+def test_process_host_equals_device_batch(eng, chunk):
+    # host-streamed ingest (copy of chunk k overlapping the processing of
+    # chunk k-1) gives exactly the one-call result, ragged last chunk included
+    n, per, cap, tcap = 64, 5000, 100, 5000
+    msgs, off = lobgen.generate(lobgen.make_params(4321, "pm1"), [per] * n)
+    ref = eng.Engine(n, cap, tcap)
+    ref.process_batch(eng.messages_to_device(msgs), torch.from_numpy(off).cuda())
+    want = gpu_outputs(ref)
+    ref.close()
+    h = torch.from_numpy(msgs.view(np.int32).reshape(-1, 8)).pin_memory()
+    e = eng.Engine(n, cap, tcap)
+    for _ in range(2):  # the second call reuses the staging buffers
+        e.reset()
+        e.process_host(h, per, chunk)
+        assert_same(gpu_outputs(e), want)
+    e.process_host(h[: n * 0], 0, chunk)  # nothing to do
+    e.reset()
+    e.process_host(h, per, 2 * chunk)  # a larger chunk regrows the staging
+    assert_same(gpu_outputs(e), want)
+    e.close()
