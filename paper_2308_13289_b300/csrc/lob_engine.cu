@@ -88,7 +88,6 @@ struct ProcArgs {
     int32_t cap, rule, trade_cap, append, chunk, pad_;
     uint64_t wait_ns;
     int32_t* l1;  // level-1 trace [message][4], or null
-    int32_t snap;  // LOB_FLAG_SNAPSHOT_CANCELS
 };
 
 template <int K>
@@ -101,7 +100,10 @@ __host__ __device__ constexpr int warp_smem_bytes(int chunk)
 template <int K>
 constexpr int max_threads() { return K >= 4 ? 256 : 512; }
 
-template <int K, bool kTrace>
+// kTrace: also write the level-1 state after every message; kSnap: the
+// snapshot cancel rule (LOB_FLAG_SNAPSHOT_CANCELS).  Each combination is its
+// own instantiation, so the default one carries neither.
+template <int K, bool kTrace, bool kSnap>
 __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
 {
     using Book = typename BookPolicy<K>::type;
@@ -213,7 +215,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                     nb = mb[2 * i + 3];
                 }
                 apply_message<K, false>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
-                                 hb.z, hb.w, ts, tally, obs, a.snap != 0);
+                                 hb.z, hb.w, ts, tally, obs, kSnap);
                 if constexpr (kTrace) {
                     const int4 top = level1_book<K>(bk, n_bid, n_ask);
                     if (l == 0) reinterpret_cast<int4*>(a.l1)[lo + (int64_t)c * chunk + i] = top;
@@ -418,24 +420,21 @@ int k_of(int capacity)
     return 16;
 }
 
-const void* process_kernel(int K, bool trace = false)
+const void* process_kernel(int K, bool trace = false, bool snap = false)
 {
-    if (trace) {
-        switch (K) {
-        case 1: return reinterpret_cast<const void*>(&k_process<1, true>);
-        case 2: return reinterpret_cast<const void*>(&k_process<2, true>);
-        case 4: return reinterpret_cast<const void*>(&k_process<4, true>);
-        case 8: return reinterpret_cast<const void*>(&k_process<8, true>);
-        default: return reinterpret_cast<const void*>(&k_process<16, true>);
-        }
-    }
+#define LOB_PROC_K(k)                                                                  \
+    return trace ? (snap ? reinterpret_cast<const void*>(&k_process<k, true, true>)     \
+                         : reinterpret_cast<const void*>(&k_process<k, true, false>))   \
+                 : (snap ? reinterpret_cast<const void*>(&k_process<k, false, true>)    \
+                         : reinterpret_cast<const void*>(&k_process<k, false, false>))
     switch (K) {
-    case 1: return reinterpret_cast<const void*>(&k_process<1, false>);
-    case 2: return reinterpret_cast<const void*>(&k_process<2, false>);
-    case 4: return reinterpret_cast<const void*>(&k_process<4, false>);
-    case 8: return reinterpret_cast<const void*>(&k_process<8, false>);
-    default: return reinterpret_cast<const void*>(&k_process<16, false>);
+    case 1: LOB_PROC_K(1);
+    case 2: LOB_PROC_K(2);
+    case 4: LOB_PROC_K(4);
+    case 8: LOB_PROC_K(8);
+    default: LOB_PROC_K(16);
     }
+#undef LOB_PROC_K
 }
 
 int smem_per_warp(int K, int chunk)
@@ -484,15 +483,15 @@ int lob_launch_process(lob_ctx* c, const lob_msg_t* d_msgs, const int64_t* d_off
     a.pad_ = 0;
     a.wait_ns = kWaitNs;
     a.l1 = d_l1;
-    a.snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) ? 1 : 0;
+    const bool snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) != 0;
     const int W = c->warps_per_cta;
     int grid = (n_active + W - 1) / W;
     const int resident = c->num_sms * c->ctas_per_sm_eff;
     if (grid > resident) grid = resident;
     if (grid < 1) grid = 1;
     void* args[] = {&a};
-    const void* fn = process_kernel(c->K, d_l1 != nullptr);
-    if (d_l1) {
+    const void* fn = process_kernel(c->K, d_l1 != nullptr, snap);
+    if (d_l1 || snap) {  // the default instantiation was set up by configure_launch
         cudaError_t ea = lob_raise_smem_limit(fn, c->smem_per_cta);
         if (ea != cudaSuccess) return lob_cuda_fail(ea, "cudaFuncSetAttribute");
     }
@@ -1136,7 +1135,6 @@ extern "C" int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t
     a.pad_ = 0;
     a.wait_ns = kWaitNs;
     a.l1 = nullptr;
-    a.snap = 0;
     const int W = static_warps(K);
     int grid = (n_books + W - 1) / W;
     const int resident = s->num_sms * s->per_sm[k_index(K)];

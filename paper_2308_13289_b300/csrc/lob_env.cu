@@ -31,7 +31,7 @@ struct lob_env {
     EnvStateDev* d_state = nullptr;
     int chunk = 0;        // staged messages per step (msgs_per_step rounded up to 8)
     int warps = 4;
-    int per_sm = 1;
+    int per_sm_v[4] = {1, 1, 1, 1};  // resident CTAs per SM of each (trace, snap) variant
     int smem_per_cta = 0;
     int64_t launches = 0;
 };
@@ -63,7 +63,6 @@ struct EnvArgs {
     int64_t* fills;
     uint64_t wait_ns;
     int32_t* l1;  // [n_run][n_envs][msgs_per_step][4] or null
-    int32_t snap;  // LOB_FLAG_SNAPSHOT_CANCELS
     const float* actions;  // [n_run][n_envs][4] policy sizes, or null (stand-in draws)
     int32_t passive_ticks, tick;
 };
@@ -75,9 +74,10 @@ __host__ __device__ constexpr int env_warp_smem(int chunk)
            128 * 128;
 }
 
-// kTrace: the kernel also writes the level-1 state after every data message
-// (a separate instantiation, so the untraced loop carries none of that code).
-template <int K, bool kTrace>
+// kTrace: the kernel also writes the level-1 state after every data message;
+// kSnap: the snapshot cancel rule (LOB_FLAG_SNAPSHOT_CANCELS).  Separate
+// instantiations, so the default loop carries neither.
+template <int K, bool kTrace, bool kSnap>
 __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
 {
     using Book = typename BookPolicy<K>::type;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                         nb = src[2 * i + 3];
                     }
                     apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
-                                     hb.y, hb.z, hb.w, ts, tally, obs, a.snap != 0);
+                                     hb.y, hb.z, hb.w, ts, tally, obs, kSnap);
                     if (kTrace && phase == 0) {
                         const int4 top = level1_book<K>(bk, n_bid, n_ask);
                         if (l == 0)
@@ -455,11 +455,13 @@ __global__ void k_env_observe(const EnvStateDev* __restrict__ env, const Msg* __
     }
 }
 
-const void* env_kernel(int K, bool trace)
+const void* env_kernel(int K, bool trace, bool snap)
 {
 #define LOB_ENV_K(k)                                                                   \
-    return trace ? reinterpret_cast<const void*>(&k_env<k, true>)                     \
-                 : reinterpret_cast<const void*>(&k_env<k, false>)
+    return trace ? (snap ? reinterpret_cast<const void*>(&k_env<k, true, true>)         \
+                         : reinterpret_cast<const void*>(&k_env<k, true, false>))       \
+                 : (snap ? reinterpret_cast<const void*>(&k_env<k, false, true>)        \
+                         : reinterpret_cast<const void*>(&k_env<k, false, false>))
     switch (K) {
     case 1: LOB_ENV_K(1);
     case 2: LOB_ENV_K(2);
@@ -542,19 +544,13 @@ int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, vo
                       cfg->msgs_per_step);
         return LOB_E_INVAL;
     }
-    if (err == cudaSuccess)
-        err = lob_raise_smem_limit(env_kernel(K, false), e->smem_per_cta);
-    if (err == cudaSuccess)
-        err = lob_raise_smem_limit(env_kernel(K, true), e->smem_per_cta);
-    if (err == cudaSuccess) {
-        // both instantiations share the launch shape: take the smaller residency
-        int per_sm_trace = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->per_sm, env_kernel(K, false),
-                                                            32 * e->warps, e->smem_per_cta);
+    for (int v = 0; v < 4 && err == cudaSuccess; ++v) {
+        const void* fn = env_kernel(K, (v & 1) != 0, (v & 2) != 0);
+        err = lob_raise_smem_limit(fn, e->smem_per_cta);
         if (err == cudaSuccess)
-            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm_trace, env_kernel(K, true), 32 * e->warps, e->smem_per_cta);
-        if (err == cudaSuccess && per_sm_trace < e->per_sm) e->per_sm = per_sm_trace;
+            err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->per_sm_v[v], fn,
+                                                                32 * e->warps, e->smem_per_cta);
+        if (e->per_sm_v[v] < 1) e->per_sm_v[v] = 1;
     }
     if (err == cudaSuccess)
         err = cudaMalloc(&e->d_state, sizeof(EnvStateDev) * (size_t)book->cfg.n_books);
@@ -562,7 +558,6 @@ int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, vo
         delete e;
         return lob_cuda_fail(err, "lob_env_create");
     }
-    if (e->per_sm < 1) e->per_sm = 1;
     int rc = lob_env_reset(e, stream);
     if (rc != LOB_OK) {
         lob_env_destroy(e);
@@ -651,16 +646,17 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     a.fills = d_fills;
     a.wait_ns = kEnvWaitNs;
     a.l1 = d_l1;
-    a.snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) ? 1 : 0;
     a.actions = d_actions;
     a.passive_ticks = e->cfg.passive_ticks;
     a.tick = e->cfg.tick_size;
     const int W = e->warps;
     int grid = (a.n_envs + W - 1) / W;
-    const int resident = c->num_sms * e->per_sm;
+    const bool snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) != 0;
+    const int variant = (d_l1 != nullptr ? 1 : 0) | (snap ? 2 : 0);
+    const int resident = c->num_sms * e->per_sm_v[variant];
     if (grid > resident) grid = resident;
     void* args[] = {&a};
-    cudaError_t err = cudaLaunchKernel(env_kernel(c->K, d_l1 != nullptr), dim3(grid),
+    cudaError_t err = cudaLaunchKernel(env_kernel(c->K, d_l1 != nullptr, snap), dim3(grid),
                                        dim3(32 * W), args,
                                        (size_t)e->smem_per_cta, (cudaStream_t)stream);
     if (err != cudaSuccess) return lob_cuda_fail(err, "lob_env_run launch");
