@@ -129,6 +129,26 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def measured_traffic():
+    """DRAM bytes (read + write) of one headline k_process launch from the
+    committed ncu capture, or None once the kernel sources have changed since
+    the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_process_replay_1024x100k_traffic.txt")
+    try:
+        kv = dict(line.split(":", 1) for line in open(path)
+                  if ":" in line and not line.startswith("#"))
+        h = hashlib.sha256()
+        for src in kv["sources"].split():
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() != kv["sources_sha256"].strip():
+            return None
+        return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def workload_streams(name, rank):
     import lobgen
     w = lobgen.WORKLOADS[name]
@@ -344,8 +364,9 @@ def run_engine(args):
     state_bytes = 2 * n * eng_book_bytes(cap)
     alg_bytes = 32 * total_msgs + 32 * trades_per_step + state_bytes + 8 * (n + 1)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
+    traffic = measured_traffic() if args.workload == "replay_1024x100k" else None
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 5), "traffic": None, "kernel": "k_process<4>",
+            "frac": round(achieved / peak, 5), "traffic": traffic, "kernel": "k_process<4>",
             "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": int(alg_bytes),
             "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
 
