@@ -226,6 +226,41 @@ __device__ __forceinline__ void shift_in(T (&v)[K], int p, int n_after, T val)
     for (int j = 0; j < K; ++j) v[j] = nv[j];
 }
 
+// shift_in with the left neighbour's last slot already fetched
+// (prev = __shfl_up_sync(kFull, v[K - 1], 1)), so that the shuffle can be
+// issued before the insertion point is known.
+template <int K, typename T>
+__device__ __forceinline__ void shift_in_prev(T (&v)[K], int p, int n_after, T val, T prev)
+{
+    const int l = lane_id();
+    T nv[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        T left = (j == 0) ? prev : v[j - 1];
+        nv[j] = (s == p) ? val : ((s > p && s < n_after) ? left : v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = nv[j];
+}
+
+// shift_out with the right neighbour's first slot already fetched
+// (next = __shfl_down_sync(kFull, v[0], 1)).
+template <int K, typename T>
+__device__ __forceinline__ void shift_out_next(T (&v)[K], int p, int n, T next)
+{
+    const int l = lane_id();
+    T nv[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const int s = l * K + j;
+        T right = (j == K - 1) ? next : v[j + 1];
+        nv[j] = (s >= p && s < n - 1) ? right : v[j];
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) v[j] = nv[j];
+}
+
 // Shift slots [p+1, n) left by one (slot p disappears).
 template <int K, typename T>
 __device__ __forceinline__ void shift_out(T (&v)[K], int p, int n)
@@ -503,6 +538,14 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
     const int l = lane_id();
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<X>(tmp);
+    // the shift's cross-lane values do not depend on the insertion point:
+    // fetch them first so that their latency overlaps the search
+    const int32_t pv_px = __shfl_up_sync(kFull, v.px[K - 1], 1);
+    const int32_t pv_q = __shfl_up_sync(kFull, v.q[K - 1], 1);
+    const int32_t pv_oid = __shfl_up_sync(kFull, v.oid[K - 1], 1);
+    const int32_t pv_tid = __shfl_up_sync(kFull, v.tid[K - 1], 1);
+    const int32_t pv_tlo = __shfl_up_sync(kFull, v.tlo[K - 1], 1);
+    const int32_t pv_thi = __shfl_up_sync(kFull, v.thi[K - 1], 1);
     // insertion point: number of resting orders with a price at least as good
     int p = 0;
 #pragma unroll
@@ -516,16 +559,17 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
     }
     // full side: the worst order (slot cap-1) has a strictly worse price and
     // is evicted
-    const int32_t q_worst = slot_value<K>(v.q, cap - 1);
-    ctr.evicted += full ? 1 : 0;
-    ctr.evicted_qty += full ? q_worst : 0;
+    if (full) {
+        ctr.evicted += 1;
+        ctr.evicted_qty += slot_value<K>(v.q, cap - 1);
+    }
     const int n_after = full ? cap : n + 1;
-    shift_in<K>(v.px, p, n_after, P);
-    shift_in<K>(v.q, p, n_after, Q);
-    shift_in<K>(v.oid, p, n_after, oid);
-    shift_in<K>(v.tid, p, n_after, tid);
-    shift_in<K>(v.tlo, p, n_after, tlo);
-    shift_in<K>(v.thi, p, n_after, thi);
+    shift_in_prev<K>(v.px, p, n_after, P, pv_px);
+    shift_in_prev<K>(v.q, p, n_after, Q, pv_q);
+    shift_in_prev<K>(v.oid, p, n_after, oid, pv_oid);
+    shift_in_prev<K>(v.tid, p, n_after, tid, pv_tid);
+    shift_in_prev<K>(v.tlo, p, n_after, tlo, pv_tlo);
+    shift_in_prev<K>(v.thi, p, n_after, thi, pv_thi);
     bk.template release<X>(v, lane_touches<K>(p, n_after));
     n = n_after;
     ctr.rested += 1;
@@ -559,9 +603,19 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
     if (hit == 0) return;  // not live on this side: no-op (counted at the end)
     ctr.cancel_hit += 1;
     const int L = __ffs(hit) - 1;
+    // each lane picks its own candidate, so both values leave lane L at once
+    const int32_t q_mine = pick<K>(v.q, jj < 0 ? 0 : jj);
     const int j_hit = __shfl_sync(kFull, jj, L);
+    const int32_t q_old = __shfl_sync(kFull, q_mine, L);
+    // a removal's cross-lane values, fetched alongside (unused when the order
+    // stays)
+    const int32_t nx_px = __shfl_down_sync(kFull, v.px[0], 1);
+    const int32_t nx_q = __shfl_down_sync(kFull, v.q[0], 1);
+    const int32_t nx_oid = __shfl_down_sync(kFull, v.oid[0], 1);
+    const int32_t nx_tid = __shfl_down_sync(kFull, v.tid[0], 1);
+    const int32_t nx_tlo = __shfl_down_sync(kFull, v.tlo[0], 1);
+    const int32_t nx_thi = __shfl_down_sync(kFull, v.thi[0], 1);
     const int p = L * K + j_hit;
-    const int32_t q_old = __shfl_sync(kFull, pick<K>(v.q, j_hit), L);
     const int32_t q_new = q_old - Q;
     if (q_new > 0) {
         bk.template set_qty<X>(L, j_hit, p, q_new);
@@ -569,12 +623,12 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
         return;
     }
     ctr.cancelled_qty += q_old;
-    shift_out<K>(v.px, p, n);
-    shift_out<K>(v.q, p, n);
-    shift_out<K>(v.oid, p, n);
-    shift_out<K>(v.tid, p, n);
-    shift_out<K>(v.tlo, p, n);
-    shift_out<K>(v.thi, p, n);
+    shift_out_next<K>(v.px, p, n, nx_px);
+    shift_out_next<K>(v.q, p, n, nx_q);
+    shift_out_next<K>(v.oid, p, n, nx_oid);
+    shift_out_next<K>(v.tid, p, n, nx_tid);
+    shift_out_next<K>(v.tlo, p, n, nx_tlo);
+    shift_out_next<K>(v.thi, p, n, nx_thi);
     bk.template release<X>(v, lane_touches<K>(p, n - 1));
     n -= 1;
 }
@@ -1194,15 +1248,19 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
                                               Tally& ctr, Obs& obs, bool snap)
 {
     if constexpr (!kCompact) {
+        // both best prices, fetched before the dispatch so that their latency
+        // overlaps it (a limit's crossing test needs one of them)
+        const int32_t best_bid = bk.template best_px<0>();
+        const int32_t best_ask = bk.template best_px<1>();
         if (op <= OP_LIMIT_ASK) {
             if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
                 int32_t rest = Q;
-                if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), P))
+                if (n_ask > 0 && at_least<1>(best_ask, P))
                     rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
                 if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
             } else if (op == OP_LIMIT_ASK) {
                 int32_t rest = Q;
-                if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), P))
+                if (n_bid > 0 && at_least<0>(best_bid, P))
                     rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
                 if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
             }
