@@ -386,7 +386,7 @@ struct RegBook {
     // the side itself is modified in place; `tmp` is unused
     template <int X> __device__ __forceinline__ SideVec<K>& acquire(SideVec<K>&) { return s[X]; }
     template <int X> __device__ __forceinline__ void release(const SideVec<K>&, bool) {}
-    template <int X> __device__ __forceinline__ int32_t best_px() const
+    template <int X> __device__ __forceinline__ int32_t best_px(int) const
     {
         return __shfl_sync(kFull, s[X].px[0], 0);
     }
@@ -453,7 +453,7 @@ struct SmemBook {
     {
         if (touch) RegBook<K>::store_side(side<X>(), v);
     }
-    template <int X> __device__ __forceinline__ int32_t best_px() const
+    template <int X> __device__ __forceinline__ int32_t best_px(int) const
     {
         return reinterpret_cast<const int32_t*>(side<X>() + Geo<K>::PX)[0];
     }
@@ -467,14 +467,23 @@ struct SmemBook {
 
 // GroupBook: the book stays in shared memory and the add / cancel / match
 // operations walk each lane's slots in groups of four, group g of lane l
-// holding slots g*128 + 4*l + (0..3) ("group-striped": 128-bit accesses of a
-// group are conflict-free), in a loop that is not unrolled, touching only the
-// fields and groups an operation needs.  Code size and per-group cost do not
-// grow with K.  Other code may still use acquire/release (blocked mapping):
-// both mappings place slot s at index s of each field array.
+// holding indices g*128 + 4*l + (0..3) ("group-striped": 128-bit accesses of
+// a group are conflict-free), in a loop that is not unrolled, touching only
+// the fields and groups an operation needs.  A side of n orders is stored
+// worst first: the order of priority rank r sits at index n-1-r, so the top
+// of the book -- where adds, cancels and fills mostly happen -- is the end of
+// the array, and an operation moves only the orders above the one it
+// touches; consumed orders leave by shortening the side.  Code size and
+// per-group cost do not grow with K.  Code that reads a grouped side in
+// priority order maps rank r to index n-1-r (storage_index<K>).
 template <int K>
 struct GroupBook : SmemBook<K> {
     static constexpr bool kGrouped = true;
+    // the best order sits at index n-1 (see the grouped operations)
+    template <int X> __device__ __forceinline__ int32_t best_px(int n) const
+    {
+        return reinterpret_cast<const int32_t*>(this->template side<X>() + Geo<K>::PX)[n > 0 ? n - 1 : 0];
+    }
 };
 
 // Books whose two sides fit in registers cheaply (K <= 4: 2 sides x 6 words x
@@ -484,6 +493,17 @@ template <int K>
 struct BookPolicy {
     using type = typename std::conditional<(K <= 4), RegBook<K>, GroupBook<K>>::type;
 };
+
+// Whether the policy of K stores a side worst first (index = n-1-rank).
+template <int K>
+__host__ __device__ constexpr bool reversed_layout() { return !(K <= 4); }
+
+// Storage index of priority rank r in a side of n orders.
+template <int K>
+__host__ __device__ __forceinline__ int storage_index(int r, int n)
+{
+    return reversed_layout<K>() ? n - 1 - r : r;
+}
 
 __device__ __forceinline__ int64_t warp_sum64(int64_t x)
 {
@@ -849,76 +869,6 @@ __device__ __forceinline__ void sts8(int64_t* a, Q64 q)
     reinterpret_cast<longlong2*>(a)[1] = make_longlong2(q.z, q.w);
 }
 
-// New slot s = old slot s-1 for s in (p, n_after), slot p = val.
-template <class T, class V, V (*LD)(const T*), void (*ST)(T*, V)>
-__device__ __forceinline__ void g_shift_in_t(T* arr, int p, int n_after, T val)
-{
-    const int l = lane_id();
-    T carry = 0;  // old slot g*128-1: lane 31's last element of the previous group
-    const int g0 = p >> 7, g1 = (n_after - 1) >> 7;
-#pragma unroll 1
-    for (int g = g0; g <= g1; ++g) {
-        T* a = arr + g * 128 + 4 * l;
-        const V v = LD(a);
-        const T up = __shfl_up_sync(kFull, v.w, 1);
-        const T prev = l == 0 ? carry : up;
-        carry = __shfl_sync(kFull, v.w, 31);
-        const int s = g * 128 + 4 * l;
-        V nv;
-        nv.x = s == p ? val : ((s > p && s < n_after) ? prev : v.x);
-        nv.y = s + 1 == p ? val : ((s + 1 > p && s + 1 < n_after) ? v.x : v.y);
-        nv.z = s + 2 == p ? val : ((s + 2 > p && s + 2 < n_after) ? v.y : v.z);
-        nv.w = s + 3 == p ? val : ((s + 3 > p && s + 3 < n_after) ? v.z : v.w);
-        if (s + 3 >= p && s < n_after) ST(a, nv);
-    }
-}
-
-// New slot s = old slot s+1 for s in [p, n-1): slot p leaves.
-template <class T, class V, V (*LD)(const T*), void (*ST)(T*, V)>
-__device__ __forceinline__ void g_shift_out_t(T* arr, int p, int n)
-{
-    const int l = lane_id();
-    T carry = 0;  // old slot (g+1)*128: lane 0's first element of the next group
-    const int last = n - 1;
-    const int g0 = p >> 7, g1 = last >> 7;
-#pragma unroll 1
-    for (int g = g1; g >= g0; --g) {
-        T* a = arr + g * 128 + 4 * l;
-        const V v = LD(a);
-        const T dn = __shfl_down_sync(kFull, v.x, 1);
-        const T next = l == 31 ? carry : dn;
-        carry = __shfl_sync(kFull, v.x, 0);
-        const int s = g * 128 + 4 * l;
-        V nv;
-        nv.x = (s >= p && s < last) ? v.y : v.x;
-        nv.y = (s + 1 >= p && s + 1 < last) ? v.z : v.y;
-        nv.z = (s + 2 >= p && s + 2 < last) ? v.w : v.z;
-        nv.w = (s + 3 >= p && s + 3 < last) ? next : v.w;
-        if (s + 3 >= p && s < last) ST(a, nv);
-    }
-}
-
-// New slot s = old slot s+m for s in [0, n-m): the first m slots leave.
-template <int K, class T, class V, void (*ST)(T*, V)>
-__device__ __forceinline__ void g_drop_front_t(T* arr, int m, int n)
-{
-    constexpr int cmax = 32 * K - 1;
-    const int l = lane_id();
-    const int keep = n - m;
-#pragma unroll 1
-    for (int g = 0; g * 128 < keep; ++g) {
-        const int s = g * 128 + 4 * l;
-        V nv;
-        nv.x = arr[min(s + m, cmax)];
-        nv.y = arr[min(s + 1 + m, cmax)];
-        nv.z = arr[min(s + 2 + m, cmax)];
-        nv.w = arr[min(s + 3 + m, cmax)];
-        __syncwarp();
-        if (s < keep) ST(arr + s, nv);
-        __syncwarp();
-    }
-}
-
 template <int K>
 struct GSide {
     char* b;
@@ -1017,15 +967,19 @@ __device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rul
 {
     const GSide<K> sd{side};
     const int l = lane_id();
-    int cnt = 0;
+    // p = orders at least as good as P: the top p indices n-p .. n-1; count
+    // group by group from the top until a group holds one that is not
+    int p = 0;
 #pragma unroll 1
-    for (int g = 0; g * 128 < n; ++g) {
-        const int4 v = lds4(sd.px() + g * 128 + 4 * l);
+    for (int g = (n - 1) >> 7; g >= 0; --g) {
         const int s = g * 128 + 4 * l;
-        cnt += (s < n && at_least<X>(v.x, P)) + (s + 1 < n && at_least<X>(v.y, P)) +
-               (s + 2 < n && at_least<X>(v.z, P)) + (s + 3 < n && at_least<X>(v.w, P));
+        const int4 v = lds4(sd.px() + s);
+        const int c = (s < n && at_least<X>(v.x, P)) + (s + 1 < n && at_least<X>(v.y, P)) +
+                      (s + 2 < n && at_least<X>(v.z, P)) + (s + 3 < n && at_least<X>(v.w, P));
+        const int gc = (int)__reduce_add_sync(kFull, (unsigned)c);
+        p += gc;
+        if (gc < min(128, n - g * 128)) break;
     }
-    const int p = (int)__reduce_add_sync(kFull, (unsigned)cnt);
     const bool full = n >= cap;
     if (full && (rule != 0 || p >= cap)) {
         ctr.rejected += 1;
@@ -1033,35 +987,41 @@ __device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rul
         return;
     }
     if (full) {
+        // the worst order (index 0) has a strictly worse price and is evicted:
+        // every other order moves down one
         ctr.evicted += 1;
-        ctr.evicted_qty += sd.qty()[cap - 1];
+        ctr.evicted_qty += sd.qty()[0];
+        g_shift_out_all<K>(sd, 0, n);
+        n -= 1;
+        __syncwarp();
     }
-    const int n_after = full ? cap : n + 1;
+    // the new order goes below the p orders at least as good, which move up
     const int64_t tm = (int64_t)(((uint64_t)(uint32_t)thi << 32) | (uint32_t)tlo);
-    g_shift_in_all<K>(sd, p, n_after, P, Q, oid, tid, tm);
-    n = n_after;
+    g_shift_in_all<K>(sd, n - p, n + 1, P, Q, oid, tid, tm);
+    n += 1;
     ctr.rested += 1;
 }
 
-// Snapshot rule (Sec. 5.1.1): slot of the earliest order with OID <= -9000
-// resting at price P, or -1.  Out of line: it runs only on a cancel miss.
+// Snapshot rule (Sec. 5.1.1): index of the earliest (highest-priority, so
+// highest-index) order with OID <= -9000 resting at price P, or -1.  Out of
+// line: it runs only on a cancel miss.
 template <int K>
 __device__ __noinline__ int g_find_snapshot(const char* side, int n, int32_t P)
 {
     const GSide<K> sd{const_cast<char*>(side)};
     const int l = lane_id();
 #pragma unroll 1
-    for (int g = 0; g * 128 < n; ++g) {
+    for (int g = (n - 1) >> 7; g >= 0; --g) {
         const int4 v = lds4(sd.oid() + g * 128 + 4 * l);
         const int4 w = lds4(sd.px() + g * 128 + 4 * l);
         const int s = g * 128 + 4 * l;
-        int jj = (s + 3 < n && w.w == P && v.w <= kSnapshotOidMax) ? 3 : -1;
-        jj = (s + 2 < n && w.z == P && v.z <= kSnapshotOidMax) ? 2 : jj;
+        int jj = (s < n && w.x == P && v.x <= kSnapshotOidMax) ? 0 : -1;
         jj = (s + 1 < n && w.y == P && v.y <= kSnapshotOidMax) ? 1 : jj;
-        jj = (s < n && w.x == P && v.x <= kSnapshotOidMax) ? 0 : jj;
+        jj = (s + 2 < n && w.z == P && v.z <= kSnapshotOidMax) ? 2 : jj;
+        jj = (s + 3 < n && w.w == P && v.w <= kSnapshotOidMax) ? 3 : jj;
         const unsigned hit = __ballot_sync(kFull, jj >= 0);
         if (hit) {
-            const int L = __ffs(hit) - 1;
+            const int L = 31 - __clz(hit);
             return g * 128 + 4 * L + __shfl_sync(kFull, jj, L);
         }
     }
@@ -1076,7 +1036,7 @@ __device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, 
     const int l = lane_id();
     int p = -1;
 #pragma unroll 1
-    for (int g = 0; g * 128 < n; ++g) {
+    for (int g = (n - 1) >> 7; g >= 0; --g) {  // recent orders sit near the top
         const int4 v = lds4(sd.oid() + g * 128 + 4 * l);
         const int s = g * 128 + 4 * l;
         int jj = (s + 3 < n && v.w == oid) ? 3 : -1;
@@ -1102,7 +1062,7 @@ __device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, 
         return;
     }
     ctr.cancelled_qty += q_old;
-    g_shift_out_all<K>(sd, p, n);
+    g_shift_out_all<K>(sd, p, n);  // the orders above move down one
     n -= 1;
 }
 
@@ -1111,39 +1071,53 @@ __device__ __forceinline__ int32_t g_match_order(char* side, int& n, int32_t P, 
                                               int32_t oid_a, int32_t tid_a, int32_t tlo,
                                               int32_t thi, TradeSink& ts, Tally& ctr, Obs& obs)
 {
+    // The side is stored worst first, so priority order is descending index:
+    // groups from the top, lanes from 31 down, and w, z, y, x inside a lane.
     const GSide<K> sd{side};
     const int l = lane_id();
+    const int n0 = n;
+    const int g_top = (n0 - 1) >> 7;
     uint32_t consumed = 0;  // quantity filled so far (warp-uniform)
     int m = 0, nf = 0;
     const int64_t count0 = ts.count;
 #pragma unroll 1
-    for (int g = 0; g * 128 < n; ++g) {
+    for (int g = g_top; g >= 0; --g) {
         const int s = g * 128 + 4 * l;
-        const int4 vp = lds4(sd.px() + g * 128 + 4 * l);
-        const int4 vq = lds4(sd.qty() + g * 128 + 4 * l);
-        const int32_t pa[4] = {vp.x, vp.y, vp.z, vp.w};
-        const int32_t qa[4] = {vq.x, vq.y, vq.z, vq.w};
+        const int4 vp = lds4(sd.px() + s);
+        const int4 vq = lds4(sd.qty() + s);
+        const int32_t pa[4] = {vp.w, vp.z, vp.y, vp.x};
+        const int32_t qa[4] = {vq.w, vq.z, vq.y, vq.x};
         uint32_t cq[4], loc[4];
         uint32_t acc = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const bool c = s + j < n && at_least<Y>(pa[j], P);
+            const bool c = s + 3 - j < n0 && at_least<Y>(pa[j], P);
             cq[j] = c ? (uint32_t)qa[j] : 0u;
             acc = sat_add(acc, cq[j]);
             loc[j] = acc;
         }
         const uint32_t Qg = (uint32_t)Q - consumed;
+        // the group's first lane in priority order; when the fills end inside
+        // it (it covers Qg, or the lane after it does not cross) no scan is needed
+        const int lt = g == g_top ? ((n0 - 1) & 127) >> 2 : 31;
         const unsigned first_crosses = __ballot_sync(kFull, cq[0] != 0u);
-        const uint32_t acc0 = __shfl_sync(kFull, acc, 0);
-        const bool local = acc0 >= Qg || !(first_crosses & 2u);
+        const uint32_t acct = __shfl_sync(kFull, acc, lt);
+        const bool local = acct >= Qg || lt == 0 || !((first_crosses >> (lt - 1)) & 1u);
         uint32_t excl, total;
         if (local) {
-            excl = l == 0 ? 0u : Qg;
-            total = acc0;
+            excl = l == lt ? 0u : Qg;
+            total = acct;
         } else {
-            const uint2 et = warp_scan_sat(acc);
-            excl = et.x;
-            total = et.y;
+            // saturating scan over the lanes above: incl(l) = sum of lanes >= l
+            uint32_t incl = acc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_down_sync(kFull, incl, d);
+                if (l + d < 32) incl = sat_add(incl, t);
+            }
+            excl = __shfl_down_sync(kFull, incl, 1);
+            if (l == 31) excl = 0;
+            total = __shfl_sync(kFull, incl, 0);
         }
         int32_t fill[4];
         unsigned nfull = 0, nfill = 0;
@@ -1157,7 +1131,7 @@ __device__ __forceinline__ int32_t g_match_order(char* side, int& n, int32_t P, 
         }
         int gm, gnf;
         if (local) {
-            const unsigned packed = __shfl_sync(kFull, nfull | (nfill << 16), 0);
+            const unsigned packed = __shfl_sync(kFull, nfull | (nfill << 16), lt);
             gm = (int)(packed & 0xffffu);
             gnf = (int)(packed >> 16);
         } else {
@@ -1166,13 +1140,14 @@ __device__ __forceinline__ int32_t g_match_order(char* side, int& n, int32_t P, 
         }
         const uint32_t gF = min(total, Qg);
         if (gnf > 0) {
-            const int4 vo = lds4(sd.oid() + g * 128 + 4 * l);
-            const int4 vt = lds4(sd.tid() + g * 128 + 4 * l);
-            const int32_t oa[4] = {vo.x, vo.y, vo.z, vo.w};
-            const int32_t ta[4] = {vt.x, vt.y, vt.z, vt.w};
+            const int4 vo = lds4(sd.oid() + s);
+            const int4 vt = lds4(sd.tid() + s);
+            const int32_t oa[4] = {vo.w, vo.z, vo.y, vo.x};
+            const int32_t ta[4] = {vt.w, vt.z, vt.y, vt.x};
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int64_t idx = count0 + s + j;
+                // trade k is the order of priority rank k
+                const int64_t idx = count0 + (n0 - 1 - (s + 3 - j));
                 if (fill[j] > 0 && idx < ts.cap) {
                     int4* dst = reinterpret_cast<int4*>(ts.log + idx);
                     dst[0] = make_int4(pa[j], fill[j], oid_a, oa[j]);
@@ -1181,25 +1156,18 @@ __device__ __forceinline__ int32_t g_match_order(char* side, int& n, int32_t P, 
             }
             obs.template on_fills<4>(fill, pa, ta, tid_a);
             if (fill[0] | fill[1] | fill[2] | fill[3])
-                sts4(sd.qty() + g * 128 + 4 * l,
-                     make_int4(qa[0] - fill[0], qa[1] - fill[1], qa[2] - fill[2], qa[3] - fill[3]));
+                sts4(sd.qty() + s,
+                     make_int4(qa[3] - fill[3], qa[2] - fill[2], qa[1] - fill[1], qa[0] - fill[0]));
         }
         consumed += gF;
         m += gm;
         nf += gnf;
-        if (gm < 128 || consumed >= (uint32_t)Q) break;
+        if (gm < min(128, n0 - g * 128) || consumed >= (uint32_t)Q) break;
     }
     __syncwarp();
     ts.count += nf;
     ctr.traded_qty += consumed;
-    if (m > 0) {
-        g_drop_front_t<K, int32_t, int4, sts4>(sd.px(), m, n);
-        g_drop_front_t<K, int32_t, int4, sts4>(sd.qty(), m, n);
-        g_drop_front_t<K, int32_t, int4, sts4>(sd.oid(), m, n);
-        g_drop_front_t<K, int32_t, int4, sts4>(sd.tid(), m, n);
-        g_drop_front_t<K, int64_t, Q64, sts8>(sd.tm(), m, n);
-        n -= m;
-    }
+    n -= m;  // the m fully filled orders were the top of the side
     return Q - (int32_t)consumed;
 }
 
@@ -1250,8 +1218,8 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
     if constexpr (!kCompact) {
         // both best prices, fetched before the dispatch so that their latency
         // overlaps it (a limit's crossing test needs one of them)
-        const int32_t best_bid = bk.template best_px<0>();
-        const int32_t best_ask = bk.template best_px<1>();
+        const int32_t best_bid = bk.template best_px<0>(n_bid);
+        const int32_t best_ask = bk.template best_px<1>(n_ask);
         if (op <= OP_LIMIT_ASK) {
             if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
                 int32_t rest = Q;
@@ -1291,13 +1259,13 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
             int32_t rest = Q;
             if (op == OP_LIMIT_BID || op == OP_MARKET_BID) {
                 const int32_t Pm = market ? kMaxInt : P;
-                if (n_ask > 0 && at_least<1>(bk.template best_px<1>(), Pm))
+                if (n_ask > 0 && at_least<1>(bk.template best_px<1>(n_ask), Pm))
                     rest = match_order<K, 1>(bk, n_ask, Pm, rest, oid, tid, tlo, thi, ts, ctr, obs);
                 if (!market && rest > 0)
                     add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
             } else {
                 const int32_t Pm = market ? 0 : P;
-                if (n_bid > 0 && at_least<0>(bk.template best_px<0>(), Pm))
+                if (n_bid > 0 && at_least<0>(bk.template best_px<0>(n_bid), Pm))
                     rest = match_order<K, 0>(bk, n_bid, Pm, rest, oid, tid, tlo, thi, ts, ctr, obs);
                 if (!market && rest > 0)
                     add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
@@ -1353,6 +1321,32 @@ __device__ __forceinline__ void emit_levels(const int32_t (&px)[K], const int32_
     __syncwarp();
 }
 
+// Prices and quantities of side X in the lane-blocked priority order the
+// level code reads (lane l: ranks l*K .. l*K+K-1); ranks >= n are undefined.
+template <int K, int X, class Book>
+__device__ __forceinline__ void priority_px_q(Book& bk, int n, int32_t (&px)[K], int32_t (&q)[K])
+{
+    if constexpr (Book::kInRegisters) {
+        SideVec<K> tmp;
+        const SideVec<K>& v = bk.template acquire<X>(tmp);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            px[j] = v.px[j];
+            q[j] = v.q[j];
+        }
+    } else {
+        const GSide<K> sd{bk.template side<X>()};
+        const int l = lane_id();
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const int r = l * K + j;
+            const int i = r < n ? storage_index<K>(r, n) : 0;
+            px[j] = sd.px()[i];
+            q[j] = sd.qty()[i];
+        }
+    }
+}
+
 // Level-1 state of both sides (Sec. 5.2.1): the best price and the summed
 // quantity of the orders at it (the level-0 prefix of each sorted side),
 // (-1, 0) for an empty side, quantity saturating at INT32_MAX.  The result is
@@ -1360,12 +1354,13 @@ __device__ __forceinline__ void emit_levels(const int32_t (&px)[K], const int32_
 template <int K>
 __device__ __forceinline__ void level1_scan(const char* side, int n, int32_t& p, int64_t& q)
 {
+    // grouped side, stored worst first: the best level is the top of the array
     const int32_t* px = reinterpret_cast<const int32_t*>(side + Geo<K>::PX);
     const int32_t* qt = reinterpret_cast<const int32_t*>(side + Geo<K>::QTY);
-    p = px[0];
+    p = px[n - 1];
     q = 0;
 #pragma unroll 1
-    for (int i = 0; i < n && px[i] == p; ++i) q += qt[i];
+    for (int i = n - 1; i >= 0 && px[i] == p; --i) q += qt[i];
 }
 
 template <int K, class Book>

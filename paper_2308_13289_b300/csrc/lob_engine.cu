@@ -298,13 +298,16 @@ __global__ void k_levels(const char* __restrict__ state, const int32_t* __restri
         const char* side = state + (int64_t)b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
         const int32_t* px = reinterpret_cast<const int32_t*>(side + Geo<K>::PX);
         const int32_t* q = reinterpret_cast<const int32_t*>(side + Geo<K>::QTY);
+        const int n = counts[2 * b + x];
         int32_t vpx[K], vq[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            vpx[j] = px[l * K + j];
-            vq[j] = q[l * K + j];
+        for (int j = 0; j < K; ++j) {  // priority rank l*K + j
+            const int r = l * K + j;
+            const int i = r < n ? storage_index<K>(r, n) : 0;
+            vpx[j] = px[i];
+            vq[j] = q[i];
         }
-        emit_levels<K>(vpx, vq, counts[2 * b + x], depth, lq[w], lp[w],
+        emit_levels<K>(vpx, vq, n, depth, lq[w], lp[w],
                        (x == 0 ? bid_px : ask_px) + (int64_t)b * depth,
                        (x == 0 ? bid_qty : ask_qty) + (int64_t)b * depth);
     }
@@ -324,12 +327,14 @@ __global__ void k_get_book(const char* __restrict__ state, const int32_t* __rest
     const int x = (int)(bx & 1);
     const int64_t b = bx >> 1;
     const char* side = state + b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
-    const bool live = s < counts[bx];
-    if (px) px[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::PX)[s] : -1;
-    if (qty) qty[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::QTY)[s] : -1;
-    if (oid) oid[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::OID)[s] : -1;
-    if (tid) tid[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::TID)[s] : -1;
-    if (tm) tm[i] = live ? reinterpret_cast<const int64_t*>(side + Geo<K>::TM)[s] : -1;
+    const int n = counts[bx];
+    const bool live = s < n;
+    const int k = live ? storage_index<K>(s, n) : 0;  // priority rank s
+    if (px) px[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::PX)[k] : -1;
+    if (qty) qty[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::QTY)[k] : -1;
+    if (oid) oid[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::OID)[k] : -1;
+    if (tid) tid[i] = live ? reinterpret_cast<const int32_t*>(side + Geo<K>::TID)[k] : -1;
+    if (tm) tm[i] = live ? reinterpret_cast<const int64_t*>(side + Geo<K>::TM)[k] : -1;
     if (count && s == 0) count[bx] = counts[bx];
 }
 
@@ -366,12 +371,13 @@ __global__ void k_set_book(char* state, int32_t* counts, int32_t n_books, int32_
         if (l == 0) atomicOr(status, LOB_STATUS_BAD_BOOK_LOAD);
     }
     char* side = state + b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
-    for (int s = l; s < n; s += 32) {
-        reinterpret_cast<int32_t*>(side + Geo<K>::PX)[s] = px[base + s];
-        reinterpret_cast<int32_t*>(side + Geo<K>::QTY)[s] = qty[base + s];
-        reinterpret_cast<int32_t*>(side + Geo<K>::OID)[s] = oid[base + s];
-        reinterpret_cast<int32_t*>(side + Geo<K>::TID)[s] = tid[base + s];
-        reinterpret_cast<int64_t*>(side + Geo<K>::TM)[s] = tm[base + s];
+    for (int s = l; s < n; s += 32) {  // priority rank s
+        const int k = storage_index<K>(s, n);
+        reinterpret_cast<int32_t*>(side + Geo<K>::PX)[k] = px[base + s];
+        reinterpret_cast<int32_t*>(side + Geo<K>::QTY)[k] = qty[base + s];
+        reinterpret_cast<int32_t*>(side + Geo<K>::OID)[k] = oid[base + s];
+        reinterpret_cast<int32_t*>(side + Geo<K>::TID)[k] = tid[base + s];
+        reinterpret_cast<int64_t*>(side + Geo<K>::TM)[k] = tm[base + s];
     }
     if (l == 0) counts[bx] = n;
 }

@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                     };
                     // initial mid of the episode (after the first data window)
                     if (t == 0) {
-                        const int32_t bb = n_bid > 0 ? bk.template best_px<0>() : 0;
-                        const int32_t ba = n_ask > 0 ? bk.template best_px<1>() : 0;
+                        const int32_t bb = n_bid > 0 ? bk.template best_px<0>(n_bid) : 0;
+                        const int32_t ba = n_ask > 0 ? bk.template best_px<1>(n_ask) : 0;
                         if (n_bid > 0 && n_ask > 0)
                             es.p_init = __ddiv_rn(__dadd_rn((double)bb, (double)ba), 2.0);
                         else if (n_bid > 0)
@@ -217,10 +217,10 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                     if (t < a.n_steps - 1 && a.actions != nullptr) {
                         // policy sizes at the four prices (Sec. 5.2.3), prices read
                         // once from the book after the data messages
-                        if (n_ask > 0) es.last_ask = bk.template best_px<1>();
+                        if (n_ask > 0) es.last_ask = bk.template best_px<1>(n_ask);
                         const float* av = a.actions + ((int64_t)r * a.n_envs + b) * 4;
-                        const int64_t pb = n_bid > 0 ? bk.template best_px<0>() : -1;
-                        const int64_t pa = n_ask > 0 ? bk.template best_px<1>() : -1;
+                        const int64_t pb = n_bid > 0 ? bk.template best_px<0>(n_bid) : -1;
+                        const int64_t pa = n_ask > 0 ? bk.template best_px<1>(n_ask) : -1;
                         int32_t px[4];
                         px[0] = (int32_t)pb;  // far touch
                         if (n_bid > 0 && n_ask > 0) {
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                             remaining -= q;
                         }
                     } else if (t < a.n_steps - 1) {
-                        if (n_ask > 0) es.last_ask = bk.template best_px<1>();
+                        if (n_ask > 0) es.last_ask = bk.template best_px<1>(n_ask);
                         const int64_t remaining = (int64_t)a.parent - es.submitted;
                         const int64_t steps_left = (int64_t)a.n_steps - t;
                         const int64_t target =
@@ -341,13 +341,12 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
             }
             // 5. top levels of both sides
             {
-                SideVec<K> t0;
-                SideVec<K>& vb = bk.template acquire<0>(t0);
-                emit_levels<K>(vb.px, vb.q, n_bid, a.depth, lq, lp, a.bid_px + o * a.depth,
+                int32_t vpx[K], vq[K];
+                priority_px_q<K, 0>(bk, n_bid, vpx, vq);
+                emit_levels<K>(vpx, vq, n_bid, a.depth, lq, lp, a.bid_px + o * a.depth,
                                a.bid_qty + o * a.depth);
-                SideVec<K> t1;
-                SideVec<K>& va = bk.template acquire<1>(t1);
-                emit_levels<K>(va.px, va.q, n_ask, a.depth, lq, lp, a.ask_px + o * a.depth,
+                priority_px_q<K, 1>(bk, n_ask, vpx, vq);
+                emit_levels<K>(vpx, vq, n_ask, a.depth, lq, lp, a.ask_px + o * a.depth,
                                a.ask_qty + o * a.depth);
             }
             __syncwarp();
