@@ -373,10 +373,11 @@ __device__ __forceinline__ bool at_least(int32_t a, int32_t p)
 // ------------------------------------------------------- storage policies
 //
 // RegBook: both sides stay in registers for a whole message stream (each lane
-// keeps its K slots of every field); used when 2*6*K registers fit (K <= 8).
-// SmemBook: both sides stay in shared memory and each operation moves the
-// lane's slots through registers; used for the largest capacity (K = 16).
-// The book operations below are written once against either policy.
+// keeps its K slots of every field, blocked: lane l holds ranks l*K..l*K+K-1);
+// used for K <= 4.  SmemBook: the staged image in shared memory, a lane's
+// slots moved through registers on demand (acquire/release); the base of
+// GroupBook (K = 8, 16), whose own operations work group by group in place.
+// The book operations below are written once against these policies.
 
 template <int K>
 struct RegBook {
