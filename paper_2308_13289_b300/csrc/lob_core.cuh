@@ -1280,22 +1280,21 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
 // Top `depth` price levels of one side whose lane vectors are px/q with n
 // live slots (Sec. 5.1.1 ten-level state): level k = k-th distinct price in
 // priority order with the summed quantity of its orders (saturating at
-// INT32_MAX); missing levels are (-1, 0).  lq/lp: per-warp shared scratch of
-// `depth` entries.
+// INT32_MAX); missing levels are (-1, 0).  The quantity of a level is the
+// difference of two prefix sums: its first order stores the exclusive prefix
+// (and the price), its last order the inclusive prefix, so no atomics are
+// needed.  lq/lp: per-warp shared scratch of `depth` entries (lq holds two
+// 64-bit words per level).
 template <int K>
 __device__ __forceinline__ void emit_levels(const int32_t (&px)[K], const int32_t (&q)[K], int n,
                                             int depth, unsigned long long* lq, int32_t* lp,
                                             int32_t* out_px, int32_t* out_q)
 {
     const int l = lane_id();
-    for (int k = l; k < depth; k += 32) {
-        lq[k] = 0;
-        lp[k] = -1;
-    }
-    __syncwarp();
     const int32_t prev = __shfl_up_sync(kFull, px[K - 1], 1);
     bool start[K];
-    int before = 0;
+    int before = 0, levels = 0;
+    long long lane_sum = 0;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int s = l * K + j;
@@ -1303,21 +1302,39 @@ __device__ __forceinline__ void emit_levels(const int32_t (&px)[K], const int32_
         start[j] = s < n && (s == 0 || px[j] != left);
         const unsigned bal = __ballot_sync(kFull, start[j]);
         before += __popc(bal & ((1u << l) - 1u));
+        levels += __popc(bal);
+        lane_sum += s < n ? q[j] : 0;
     }
+    // warp exclusive prefix of the lane sums (64-bit: exact for any side)
+    long long incl = lane_sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const long long t = __shfl_up_sync(kFull, incl, d);
+        if (l >= d) incl += t;
+    }
+    long long pre = incl - lane_sum;
+    // a slot ends its level when the next slot starts one (or it is the last)
+    const bool next_lane_start = __shfl_down_sync(kFull, start[0] ? 1 : 0, 1) != 0;
     int lvl = before - 1;
 #pragma unroll
     for (int j = 0; j < K; ++j) {
         const int s = l * K + j;
         lvl += start[j] ? 1 : 0;
-        if (s < n && lvl < depth) {
-            atomicAdd(&lq[lvl], (unsigned long long)q[j]);
-            if (start[j]) lp[lvl] = px[j];
+        const bool nxt = j + 1 < K ? start[j + 1] : next_lane_start;
+        const bool end = s < n && (s == n - 1 || nxt);
+        if (start[j] && lvl < depth) {
+            lq[2 * lvl] = (unsigned long long)pre;
+            lp[lvl] = px[j];
         }
+        pre += s < n ? q[j] : 0;
+        if (end && lvl < depth) lq[2 * lvl + 1] = (unsigned long long)pre;
     }
     __syncwarp();
     for (int k = l; k < depth; k += 32) {
-        out_px[k] = lp[k];
-        out_q[k] = (int32_t)min(lq[k], (unsigned long long)kMaxInt);
+        const bool have = k < levels;
+        out_px[k] = have ? lp[k] : -1;
+        out_q[k] = have ? (int32_t)min((long long)(lq[2 * k + 1] - lq[2 * k]), (long long)kMaxInt)
+                        : 0;
     }
     __syncwarp();
 }

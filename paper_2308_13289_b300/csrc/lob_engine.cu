@@ -289,7 +289,7 @@ __global__ void k_levels(const char* __restrict__ state, const int32_t* __restri
                          int32_t n_books, int32_t depth, int32_t* bid_px, int32_t* bid_qty,
                          int32_t* ask_px, int32_t* ask_qty)
 {
-    __shared__ unsigned long long lq[8][64];
+    __shared__ unsigned long long lq[8][128];
     __shared__ int32_t lp[8][64];
     const int l = lane_id(), w = threadIdx.x >> 5;
     const int b = blockIdx.x * (blockDim.x >> 5) + w;

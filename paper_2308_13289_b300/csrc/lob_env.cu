@@ -39,7 +39,7 @@ struct lob_env {
 namespace {
 
 constexpr uint64_t kEnvWaitNs = 2000000000ull;
-constexpr int kLevelScratch = 64 * 8 + 64 * 4;
+constexpr int kLevelScratch = 128 * 8 + 64 * 4;  // two prefix words and a price per level
 constexpr int kAgentRecs = 8;  // staged agent orders of one step (at most 4 + 1)
 
 struct EnvArgs {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
     char* msgbuf = base + Geo<K>::BOOK_BYTES;
     uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk * 32);
     unsigned long long* lq = reinterpret_cast<unsigned long long*>(msgbuf + 2 * chunk * 32 + 16);
-    int32_t* lp = reinterpret_cast<int32_t*>(lq + 64);
+    int32_t* lp = reinterpret_cast<int32_t*>(lq + 128);
     int4* agent_buf = reinterpret_cast<int4*>(lp + 64);
     const int total_warps = gridDim.x * W;
     const uint32_t bytes = (uint32_t)a.msgs_per_step * 32;
