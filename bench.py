@@ -353,6 +353,8 @@ def run_engine(args):
                "bit_exact_vs_persistent": all(
                    torch.equal(x, y) for x, y in zip(before, snapshot_results(e, depth)))}
 
+    overflow = overflow_stats(e)
+
     # ---------------- parity on a sample of books + CPU baseline (rank 0 only)
     cpu = parity = None
     if rank == 0 and args.oracle_books > 0:
@@ -396,7 +398,7 @@ def run_engine(args):
                 "plain": plain, "plain_graph": plain_graph,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "parity": parity,
-                "device_status": status, "workloads": extras}
+                "overflow": overflow, "device_status": status, "workloads": extras}
         print(json.dumps(line))
     e.close()
     if world > 1:
@@ -484,8 +486,11 @@ def run_uneven(args, rank):
     params = lobgen.make_params(w["seed"], w["mid_walk"])
     ids = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
     tcap = trade_capacity_for(counts)
+    import hashlib
     res = {"n_books": n, "messages": int(counts.sum()), "count_min": int(counts.min()),
-           "count_max": int(counts.max()), "count_mean": float(counts.mean())}
+           "count_max": int(counts.max()), "count_mean": float(counts.mean()),
+           "counts_sha256": hashlib.sha256(counts.astype("<i8").tobytes()).hexdigest(),
+           "seed": w["seed"]}
     for order in ("natural", "longest_first"):
         perm = np.arange(n) if order == "natural" else np.argsort(-counts, kind="stable")
         gen = lobgen.DeviceStreams(params, n, stream_ids=ids)
@@ -516,6 +521,7 @@ def run_uneven(args, rank):
             ok &= np.array_equal(ctr[sample].cpu().numpy(), o.counters())
             res["parity"] = {"books_checked": int(len(sample)), "bit_exact": bool(ok),
                              "device_status": int(st.item())}
+            res["overflow"] = overflow_stats(e)
         e.close()
         del dm, doff, gen
     return res
@@ -559,7 +565,7 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
         st, p0 = env.state()
         return [v.clone() for v in out.values()] + [st, p0] + list(e.book().values())
 
-    res = {"n_envs": n, "steps": steps, "msgs_per_step": per}
+    res = {"n_envs": n, "steps": steps, "msgs_per_step": per, "seed": w["seed"]}
     ref = None
     forms = {}
     for name, fn in (("per_step_launches", per_step), ("persistent_episode", persistent)):
@@ -599,6 +605,7 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
     res["graph_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snapshot()))
     del g
     std_out = {k: v.cpu().numpy() for k, v in out.items()}  # the stand-in agent's episode
+    res["overflow"] = overflow_stats(e)
     # policy loop (Sec. 5.2.2-5.2.3): every step acts on four sizes and ends
     # with the step's level-1 trace and the observation vector, as a policy in
     # the loop needs; the sizes are seeded stand-ins for a policy's output
@@ -698,6 +705,7 @@ def run_serving(args, rank):
     rep["offered_msgs_per_s"] = round(sum(e.n_steps * e.msgs_per_step for e in eps)
                                       / args.serving_window, 1)
     rep["window_s"] = args.serving_window
+    rep["seed"] = w["seed"] + rank
     for k in ("wall_s", "steps_per_s", "msgs_per_s", "p50_step_ms", "p99_step_ms"):
         rep[k] = round(rep[k], 4)
     return rep
@@ -731,6 +739,17 @@ def time_steps(fn, args, stream, barrier, world, steps=None):
     barrier()
     ms = max_over_ranks(a.elapsed_time(b), world) / steps
     return {"ms_per_step": round(ms, 4)}
+
+
+def overflow_stats(e):
+    """Fraction of messages that met the full-side rule (Sec. 4 overflow
+    reading: rejected or evicting), from the engine's own counters."""
+    import paper_2308_13289_b300 as eng
+    ctr = e.stats()[0].sum(dim=0).cpu().numpy()
+    c = dict(zip(eng.COUNTERS, (int(x) for x in ctr)))
+    hits = c["rejected"] + c["evicted"]
+    return {"full_side_rule_fraction": round(hits / max(1, c["msgs"]), 5),
+            "rejected": c["rejected"], "evicted": c["evicted"], "messages": c["msgs"]}
 
 
 def snapshot_results(e, depth):
