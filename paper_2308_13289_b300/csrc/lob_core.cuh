@@ -209,26 +209,9 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
 
 // ---------------------------------------------------------------- primitives
 
-// Shift slots [p, n_after) right by one and place `val` at slot p.
-template <int K, typename T>
-__device__ __forceinline__ void shift_in(T (&v)[K], int p, int n_after, T val)
-{
-    const int l = lane_id();
-    T prev = __shfl_up_sync(kFull, v[K - 1], 1);
-    T nv[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const int s = l * K + j;
-        T left = (j == 0) ? prev : v[j - 1];
-        nv[j] = (s == p) ? val : ((s > p && s < n_after) ? left : v[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < K; ++j) v[j] = nv[j];
-}
-
-// shift_in with the left neighbour's last slot already fetched
-// (prev = __shfl_up_sync(kFull, v[K - 1], 1)), so that the shuffle can be
-// issued before the insertion point is known.
+// Shift slots [p, n_after) right by one and place `val` at slot p, with the
+// left neighbour's last slot already fetched (prev = __shfl_up_sync(kFull,
+// v[K - 1], 1)), so that the shuffle can be issued before p is known.
 template <int K, typename T>
 __device__ __forceinline__ void shift_in_prev(T (&v)[K], int p, int n_after, T val, T prev)
 {
@@ -832,23 +815,6 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
     return Q - F;
 }
 
-
-// Warp exclusive prefix and total of the lane values (saturating at INT32_MAX:
-// exact wherever the running total is below Q <= INT32_MAX, which is all that
-// the fills depend on).
-static __device__ __noinline__ uint2 warp_scan_sat(uint32_t acc)
-{
-    const int l = lane_id();
-    uint32_t incl = acc;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, d);
-        if (l >= d) incl = sat_add(incl, t);
-    }
-    uint32_t excl = __shfl_up_sync(kFull, incl, 1);
-    if (l == 0) excl = 0;
-    return make_uint2(excl, __shfl_sync(kFull, incl, 31));
-}
 
 // ------------------------------------------------------- grouped operations
 //
