@@ -173,7 +173,8 @@ def _oracle_episode(m, n_env, n_steps, per, actions, cap, tcap, parent, ticks, t
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("cap,per,ticks,tick", [(7, 40, 2, 1), (100, 100, 3, 1), (250, 64, 1, 5)])
+@pytest.mark.parametrize("cap,per,ticks,tick", [(7, 40, 2, 1), (100, 100, 3, 1), (250, 64, 1, 5),
+                                                (33, 37, 2, 1)])
 def test_gpu_action_steps_and_observations_match_oracle(cap, per, ticks, tick):
     import torch
 
