@@ -20,8 +20,10 @@ fills and the VWAP reward of eqs. rewardfunc / vwap).
 
 Parity status: matching, cancel, dispatch, levels and the canonical dump are
 pinned by hand-worked examples, closed forms, invariants and the brute-force
-cross-check; the full-side rule, the trade-log bound, the synthetic agent and
-the reward's handling of empty steps are readings of silent passages, pinned
+cross-check; the full-side rule, the trade-log bound, the synthetic agent, the
+reward's handling of empty steps, the snapshot OIDs' order and the <= -9000
+reading, the action map's rounding and sizing, and the observation's values
+for a missing side are readings of silent or conflicting passages, pinned
 only by hand-worked examples (parity against the paper itself unpinned there).
 """
 from __future__ import annotations

@@ -32,7 +32,12 @@
 //   otherwise rejects the residual (or always rejects, rule 1); trades beyond
 //   the per-call log capacity are executed but not stored; trade records carry
 //   both trader ids; type 0 is padding; malformed messages are counted and
-//   skipped.
+//   skipped.  Execution environment (Sec. 5.2): the seeded stand-in agent, the
+//   reward of an empty step, the snapshot OIDs' order and the <= -9000 cancel
+//   reading, the action map's rounding (mid up to the tick grid) and sizing
+//   (whole shares, task cap), and -1 for observation values of a missing side.
+//   Parity unpinned against the paper for these readings: hand-worked
+//   examples of the reading pin them.
 //
 // Data structure: per side an ordered map price -> FIFO queue of orders, and
 // a hash map from live OID to its price.
