@@ -251,3 +251,45 @@ def test_process_host_equals_device_batch(eng, chunk):
     e.process_host(h, per, 2 * chunk)  # a larger chunk regrows the staging
     assert_same(gpu_outputs(e), want)
     e.close()
+
+
+def test_clear_trades_and_reset_books_mid_stream(eng):
+    # two halves of every book's stream with appended trade logs; between them
+    # the logs are cleared and a subset of books is emptied (a serving slot
+    # handed to a new episode): those restart from empty on the second half
+    n, per, cap, tcap = 12, 3000, 100, 4000
+    msgs, off = lobgen.generate(lobgen.make_params(8080, "pm1"), [per] * n)
+    half = per // 2
+    first = np.concatenate([msgs[off[b]:off[b] + half] for b in range(n)])
+    second = np.concatenate([msgs[off[b] + half:off[b + 1]] for b in range(n)])
+    o1 = np.arange(0, n * half + 1, half, dtype=np.int64)
+    o2 = np.arange(0, n * (per - half) + 1, per - half, dtype=np.int64)
+    reset = np.array([1, 4, 5, 11], np.int32)
+    keep = np.setdiff1d(np.arange(n), reset)
+
+    e = eng.Engine(n, cap, tcap, append_trades=True)
+    launches0 = eng.lob_launch_count(e.h)
+    e.process_batch(eng.messages_to_device(first), torch.from_numpy(o1).cuda())
+    e.clear_trades()
+    e.reset_books(torch.from_numpy(reset).cuda())
+    e.process_batch(eng.messages_to_device(second), torch.from_numpy(o2).cuda())
+    g = gpu_outputs(e)
+    assert eng.lob_launch_count(e.h) >= launches0 + 2
+    e.close()
+
+    # kept books: both halves, logs cleared in between; counters of both halves
+    ok = oracle.Oracle(n, cap, tcap, append_trades=True)
+    ok.process(first, o1)
+    ok.clear_trades()
+    ok.process(second, o2)
+    rk = oracle_outputs(ok)
+    # reset books: the second half alone, from empty, with fresh counters
+    orr = oracle.Oracle(n, cap, tcap, append_trades=True)
+    orr.process(second, o2)
+    rr = oracle_outputs(orr)
+    for key in rk:
+        if key == "status":
+            assert g["status"] == 0
+            continue
+        assert np.array_equal(g[key][keep], rk[key][keep]), key
+        assert np.array_equal(g[key][reset], rr[key][reset]), key
