@@ -431,6 +431,14 @@ int64_t lob_launch_count(const lob_ctx* ctx);
 const char* lob_last_error(void);
 
 /* Library ABI version (incremented on incompatible change). */
+/* Failure handling self-test (no counterpart in the paper): run the bounded
+ * wait that guards every staged copy on an mbarrier that nothing completes,
+ * for limit_ns (1 ns .. 1 s).  The wait gives up as designed, OR-s
+ * LOB_STATUS_TIMEOUT into *d_status (int32, device) and, when d_elapsed_ns is
+ * non-null, stores the nanoseconds it waited (uint64, device).  No fault, no
+ * hang: the device stays usable.  LOB_E_INVAL on a bad argument. */
+int lob_selftest_wait(int64_t limit_ns, int32_t* d_status, uint64_t* d_elapsed_ns, void* stream);
+
 int lob_abi_version(void);
 
 #ifdef __cplusplus

@@ -114,6 +114,11 @@ def _host_ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def lob_selftest_wait(limit_ns, status, elapsed=None, stream=None):
+    check(lib().lob_selftest_wait(int(limit_ns), _ptr(status), _ptr(elapsed), _stream(stream)),
+          "lob_selftest_wait")
+
+
 def lob_process_host(h, h_msgs, msgs_per_book, chunk_msgs, stream=None):
     check(lib().lob_process_host(h, _host_ptr(h_msgs), int(msgs_per_book), int(chunk_msgs),
                                  _stream(stream)), "lob_process_host")

@@ -48,6 +48,7 @@ SIGNATURES = {
     "lob_env_run": (ctypes.c_int, [vp, vp, i64, i32, i32] + [vp] * 9 + [vp]),
     "lob_env_observe": (ctypes.c_int, [vp, vp, i64, vp, vp, vp]),
     "lob_process_host": (ctypes.c_int, [vp, vp, i64, i32, vp]),
+    "lob_selftest_wait": (ctypes.c_int, [i64, vp, vp, vp]),
     "lob_literal_process": (ctypes.c_int, [vp, vp, i32, i32, i32, i32, i32] + [vp] * 8 + [vp]),
     "lob_env_get_state": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_last_error": (ctypes.c_char_p, []),

@@ -545,6 +545,41 @@ static int configure_launch(lob_ctx* c, int W, int chunk, int ctas_per_sm)
 
 extern "C" {
 
+namespace {
+
+// Self-test of the bounded wait that guards every staged copy: an mbarrier
+// that nothing will ever complete, waited on for limit_ns; running out of
+// time sets LOB_STATUS_TIMEOUT, as a late copy does in the processing kernels.
+__global__ void k_wait_selftest(uint64_t limit_ns, int32_t* status, uint64_t* elapsed_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncwarp();
+    const uint64_t t0 = global_ns();
+    const bool done = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (threadIdx.x == 0) {
+        if (!done) atomicOr(status, LOB_STATUS_TIMEOUT);
+        if (elapsed_ns) *elapsed_ns = global_ns() - t0;
+    }
+}
+
+}  // namespace
+
+int lob_selftest_wait(int64_t limit_ns, int32_t* d_status, uint64_t* d_elapsed_ns, void* stream)
+{
+    if (limit_ns < 1 || limit_ns > 1000000000LL || !d_status) {
+        lob_set_error("lob_selftest_wait: limit must be 1 ns .. 1 s and d_status non-null");
+        return LOB_E_INVAL;
+    }
+    k_wait_selftest<<<1, 32, 0, (cudaStream_t)stream>>>((uint64_t)limit_ns, d_status,
+                                                        d_elapsed_ns);
+    const cudaError_t err = cudaGetLastError();
+    return err == cudaSuccess ? LOB_OK : lob_cuda_fail(err, "lob_selftest_wait");
+}
+
 int lob_abi_version(void) { return 2; }
 
 const char* lob_last_error(void) { return g_err.c_str(); }

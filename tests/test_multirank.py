@@ -56,3 +56,43 @@ def test_balanced_ranges_cover_books_once():
 
 def test_single_process_max_is_identity():
     assert ldist.max_over_ranks(3.5) == 3.5
+
+
+def _failing_worker(rank, world, port, q):
+    # rank 1 fails between steps (before the timing reduction); rank 0 must
+    # learn it from the process group's timeout, not hang
+    import datetime
+
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        q.put((1, "left"))
+        q.close()
+        q.join_thread()
+        os._exit(3)  # the failing rank leaves with its collective not entered
+    try:
+        ldist.max_over_ranks(1.0)
+        q.put((0, "no error"))
+    except Exception as exc:  # a timeout or connection error from gloo
+        q.put((0, type(exc).__name__))
+    q.close()
+    q.join_thread()
+    os._exit(0)
+
+
+def test_rank_failure_surfaces_as_an_error_not_a_hang():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_failing_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1] == "left"
+    assert res[0] != "no error", res
+    assert procs[0].exitcode == 0 and procs[1].exitcode == 3
