@@ -810,6 +810,16 @@ def cpu_baseline_and_parity(e, msgs, off, counts, cap, tcap, depth, n_sample, w)
                      % (n_sample, len(counts), "{:,}".format(int(counts[0])) if
                         (counts == counts[0]).all() else "lognormal", n_msgs),
            "seconds": round(dt, 3), "cpu_model": cpu_model()}
+    # the same oracle on one thread, over the first 16 books
+    n1 = min(16, n_sample)
+    o1 = oracle.Oracle(n1, cap, tcap)
+    t = time.perf_counter()
+    o1.process(msgs[:int(off[n1])], off[:n1 + 1], threads=1)
+    dt1 = time.perf_counter() - t
+    cpu["single_thread"] = {"value": round(int(off[n1]) / dt1, 1), "unit": UNIT,
+                            "sample": "first %d books, full streams (%d messages)"
+                                      % (n1, int(off[n1])), "seconds": round(dt1, 3)}
+    del o1
     # parity
     bk = e.book()
     gl = e.levels(depth)
