@@ -242,10 +242,11 @@ def run_engine(args):
     launches0 = e.launch_count()
     torch.cuda.synchronize()
     barrier()
-    t0.record(stream)
-    for i in range(args.steps):
-        step_persistent(kev[i])
-    t1.record(stream)
+    with nvtx("persistent"):
+        t0.record(stream)
+        for i in range(args.steps):
+            step_persistent(kev[i])
+        t1.record(stream)
     torch.cuda.synchronize()
     barrier()
     launches = e.launch_count() - launches0
@@ -283,7 +284,7 @@ def run_engine(args):
                     raise eng.LobError(rc, "lob_process_batch")
             eng.lob_get_levels(ep.h, depth, *lv_out)
 
-        plain = time_steps(step_plain, args, stream, barrier, world)
+        plain = time_steps(step_plain, args, stream, barrier, world, name="plain")
         plain["launches_per_step"] = nch + 1
         # same result as the persistent form
         plain["bit_exact_vs_persistent"] = same_results(e, ep, depth)
@@ -305,7 +306,8 @@ def run_engine(args):
                         raise eng.LobError(rc, "lob_process_batch")
                 eng.lob_get_levels(ep.h, depth, *lv_out, stream=s2)
         stream.wait_stream(s2)
-        plain_graph = time_steps(lambda: g.replay(), args, stream, barrier, world)
+        plain_graph = time_steps(lambda: g.replay(), args, stream, barrier, world,
+                                 name="plain_graph")
         plain_graph["launches_per_step"] = nch + 1
         plain_graph["bit_exact_vs_persistent"] = same_results(e, ep, depth)
         del g
@@ -342,7 +344,8 @@ def run_engine(args):
                 h.copy_(d, non_blocking=True)
             h_cnt.copy_(d_cnt, non_blocking=True)
 
-        r = time_steps(step_e2e, args, stream, barrier, world, steps=max(3, args.steps // 2))
+        r = time_steps(step_e2e, args, stream, barrier, world, steps=max(3, args.steps // 2),
+                       name="e2e")
         e2e = {"value": total_msgs * world / (r["ms_per_step"] / 1e3), "unit": UNIT,
                "ms_per_step": r["ms_per_step"],
                "h2d_bytes_per_step": int(h_msgs.numel() * 4 + (0 if per_book else h_off.numel() * 8)),
@@ -377,10 +380,11 @@ def run_engine(args):
         e.close()
         del d_msgs
         torch.cuda.empty_cache()
-        extras = {"uneven_4096_lognormal": run_uneven(args, rank),
-                  "rl_exec_8192x400": run_rl(args, rank),
-                  "serving_mix": run_serving(args, rank),
-                  "ablation_paper_literal": run_ablation(args, rank)}
+        extras = {}
+        for key, fn in (("uneven_4096_lognormal", run_uneven), ("rl_exec_8192x400", run_rl),
+                        ("serving_mix", run_serving), ("ablation_paper_literal", run_ablation)):
+            with nvtx(key):
+                extras[key] = fn(args, rank)
         e = eng.Engine(1, cap, 1)
 
     if rank == 0:
@@ -739,19 +743,36 @@ def max_over_ranks(x, world):
     return x if world == 1 else ldist.max_over_ranks(x, device="cuda")
 
 
-def time_steps(fn, args, stream, barrier, world, steps=None):
+def nvtx(name):
+    """NVTX range around a bench leg (lets a profiler select it by name)."""
+    import contextlib
+
+    import torch
+
+    @contextlib.contextmanager
+    def rng():
+        torch.cuda.nvtx.range_push(name)
+        try:
+            yield
+        finally:
+            torch.cuda.nvtx.range_pop()
+    return rng()
+
+
+def time_steps(fn, args, stream, barrier, world, steps=None, name="leg"):
     import torch
     steps = steps or args.steps
-    for _ in range(args.warmup):
-        fn()
-    torch.cuda.synchronize()
-    barrier()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(steps):
-        fn()
-    b.record(stream)
-    torch.cuda.synchronize()
+    with nvtx(name):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
     barrier()
     ms = max_over_ranks(a.elapsed_time(b), world) / steps
     return {"ms_per_step": round(ms, 4)}
