@@ -114,3 +114,59 @@ def test_rl_exec_8192x400_full_size(eng):
     ost, op0 = oenv.state()
     assert np.array_equal(st.cpu().numpy()[sample], ost)
     assert p0.cpu().numpy()[sample].tobytes() == op0.tobytes()
+
+
+def test_replay_1024x100k_invariants_on_every_book(eng):
+    """Properties that hold at any size, checked on all 1,024 books and on
+    every one of the 1.024e8 level-1 trace rows (the oracle would take
+    minutes for all of them): quantity conservation per book, sides in
+    priority order with positive quantities and unique ids, no crossed book
+    after any message, trade-log totals equal to the traded quantity, and the
+    last trace row equal to the top level."""
+    w = lobgen.WORKLOADS["replay_1024x100k"]
+    n, per, cap = w["n_books"], w["msgs"], w["capacity"]
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    dm, doff = lobgen.DeviceStreams(params, n).advance([per] * n)
+    tcap = int(per * 0.75) + 1024
+    e = eng.Engine(n, cap, tcap)
+    l1 = torch.empty((n * per, 4), dtype=torch.int32, device="cuda")
+    eng.lob_process_batch_l1(e.h, dm, doff, l1)
+    bk = e.book()
+    tr, tcnt = e.trades()
+    ctr, st = e.stats()
+    bp, bq, ap, aq = e.levels(1)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    c = {k: ctr[:, i] for i, k in enumerate(eng.COUNTERS)}
+    # conservation: submitted = 2 x traded + cancelled + rejected + evicted + resting + dropped
+    live = torch.arange(cap, device="cuda")[None, None, :] < bk["count"][:, :, None].long()
+    resting = torch.where(live, bk["qty"].long(), torch.zeros_like(bk["qty"].long())).sum((1, 2))
+    lhs = c["limit_qty"] + c["market_qty"]
+    rhs = (2 * c["traded_qty"] + c["cancelled_qty"] + c["rejected_qty"] + c["evicted_qty"]
+           + resting + c["market_discarded_qty"])
+    assert torch.equal(lhs, rhs)
+    assert int(c["msgs"].sum()) == n * per
+    # sides: priority order, positive quantities, unique ids
+    px = bk["price"].long()
+    nxt_ok = torch.where(live[:, :, 1:], torch.stack([px[:, 0, :-1] >= px[:, 0, 1:],
+                                                      px[:, 1, :-1] <= px[:, 1, 1:]], 1),
+                         torch.ones_like(live[:, :, 1:]))
+    assert bool(nxt_ok.all())
+    assert bool(torch.where(live, bk["qty"] > 0, torch.ones_like(live)).all())
+    oid = torch.where(live, bk["oid"].long(), -1 - torch.arange(n * 2 * cap, device="cuda")
+                      .view(n, 2, cap))
+    assert torch.sort(oid.view(n, -1), 1).values.diff(dim=1).ne(0).all()
+    # never crossed, after any message of any book
+    both = (l1[:, 0] > 0) & (l1[:, 2] > 0)
+    assert bool((l1[:, 0][both] < l1[:, 2][both]).all())
+    assert bool(((l1[:, 0] > 0) == (l1[:, 1] > 0)).all())
+    last = l1.view(n, per, 4)[:, -1]
+    assert torch.equal(last[:, 0], bp[:, 0]) and torch.equal(last[:, 1], bq[:, 0])
+    assert torch.equal(last[:, 2], ap[:, 0]) and torch.equal(last[:, 3], aq[:, 0])
+    # every trade stored (the log holds them all here) and the totals agree
+    assert bool((tcnt <= tcap).all()) and torch.equal(tcnt, c["trades"])
+    stored = torch.arange(tcap, device="cuda")[None, :] < tcnt[:, None]
+    qty = tr[:, :, 1].long()
+    assert bool(torch.where(stored, qty > 0, torch.ones_like(stored)).all())
+    assert torch.equal(torch.where(stored, qty, torch.zeros_like(qty)).sum(1), c["traded_qty"])
+    e.close()
