@@ -124,8 +124,19 @@ def test_replay_1024x100k_invariants_on_every_book(eng):
     after any message, trade-log totals equal to the traded quantity, and the
     last trace row equal to the top level."""
     w = lobgen.WORKLOADS["replay_1024x100k"]
-    n, per, cap = w["n_books"], w["msgs"], w["capacity"]
-    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    _invariants_on_every_book(eng, w["n_books"], w["msgs"], w["capacity"], w["seed"],
+                              w["mid_walk"])
+
+
+@pytest.mark.parametrize("cap", [250, 500])
+def test_grouped_books_invariants_on_every_book(eng, cap):
+    """The same properties for books kept in shared memory (stored worst
+    first), 1,024 books x 2e4 messages."""
+    _invariants_on_every_book(eng, 1024, 20_000, cap, 4040 + cap, "pm1")
+
+
+def _invariants_on_every_book(eng, n, per, cap, seed, walk):
+    params = lobgen.make_params(seed, walk)
     dm, doff = lobgen.DeviceStreams(params, n).advance([per] * n)
     tcap = int(per * 0.75) + 1024
     e = eng.Engine(n, cap, tcap)
