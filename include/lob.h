@@ -108,7 +108,11 @@ enum {
     LOB_STATUS_TIMEOUT = 1,       /* a message chunk did not arrive within the wait bound */
     LOB_STATUS_BAD_BOOK = 2,      /* a book id outside [0, n_books) was skipped            */
     LOB_STATUS_BAD_SEGMENT = 4,   /* a segment with offsets[i+1] < offsets[i] was skipped  */
-    LOB_STATUS_BAD_BOOK_LOAD = 8  /* lob_set_book: a side not in priority order was emptied */
+    LOB_STATUS_BAD_BOOK_LOAD = 8, /* lob_set_book: a side not in priority order was emptied */
+    LOB_STATUS_CHECK = 16         /* checked builds only (-DLOB_CHECKS): after some message a
+                                     book broke an invariant (side count outside 0..capacity,
+                                     a side out of priority order, a resting quantity <= 0,
+                                     a crossed book)                                          */
 };
 
 /* per-book counters (int64), in this order */

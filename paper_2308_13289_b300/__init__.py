@@ -28,6 +28,7 @@ COUNTERS = ["msgs", "limit", "cancel", "market", "noop", "invalid", "trades", "t
             "cancelled_qty", "cancel_miss", "market_discarded_qty", "limit_qty", "market_qty",
             "trades_dropped"]
 STATUS_TIMEOUT, STATUS_BAD_BOOK, STATUS_BAD_SEGMENT, STATUS_BAD_BOOK_LOAD = 1, 2, 4, 8
+STATUS_CHECK = 16  # checked builds only
 
 MSG_DTYPE = np.dtype([("type", "<i4"), ("side", "<i4"), ("price", "<i4"), ("qty", "<i4"),
                       ("oid", "<i4"), ("tid", "<i4"), ("time_ns", "<i8")])

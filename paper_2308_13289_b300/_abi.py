@@ -5,7 +5,9 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblob.so")
+# LOB_CHECKED=1 selects the variant built with invariant checks
+LIB_PATH = os.path.join(HERE, "liblob_checked.so" if os.environ.get("LOB_CHECKED") == "1"
+                        else "liblob.so")
 
 vp = ctypes.c_void_p
 i32 = ctypes.c_int32
@@ -63,8 +65,8 @@ def load():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("liblob.so is not built; run paper_2308_13289_b300.build.build() "
-                              "(the engine has no CPU fallback)")
+            raise ImportError("%s is not built; run paper_2308_13289_b300.build.build() "
+                              "(the engine has no CPU fallback)" % os.path.basename(LIB_PATH))
         lib = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)

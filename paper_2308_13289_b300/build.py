@@ -9,6 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "liblob.so")
+# the checked variant: invariant checks after every message (-DLOB_CHECKS)
+LIB_CHECKED = os.path.join(HERE, "liblob_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
               "-ffp-contract=off", "-fmad=false"]
@@ -24,16 +26,19 @@ def _newest_input():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ into one shared library; returns its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    build_dir = os.path.join(HERE, "_build")
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every .cu under csrc/ into one shared library; returns its path.
+    checked=True builds the variant with invariant checks (liblob_checked.so)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    build_dir = os.path.join(HERE, "_build_checked" if checked else "_build")
     os.makedirs(build_dir, exist_ok=True)
     objs = []
     for src in sources():
         obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
-        cmd = ["nvcc", "-c", src, "-o", obj] + ARCH + NVCC_FLAGS
+        cmd = ["nvcc", "-c", src, "-o", obj] + ARCH + NVCC_FLAGS + \
+            (["-DLOB_CHECKS"] if checked else [])
         if verbose:
             cmd.append("-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -42,13 +47,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             print(r.stderr)
         objs.append(obj)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     r = subprocess.run(["nvcc", "-shared", "-o", tmp] + objs + ARCH, capture_output=True,
                        text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -1243,6 +1243,57 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
     if constexpr (!Book::kInRegisters) __syncwarp();
 }
 
+// Invariant check after a message, compiled only into checked builds
+// (-DLOB_CHECKS; otherwise it is empty): side counts within 0..cap, both sides
+// in priority order, resting quantities > 0, the book not crossed.  A failure
+// sets LOB_STATUS_CHECK in the status word; nothing traps.
+template <int K, class Book>
+__device__ __forceinline__ void check_book(Book& bk, int n_bid, int n_ask, int cap,
+                                           int32_t* status)
+{
+#ifdef LOB_CHECKS
+    const int l = lane_id();
+    bool bad = n_bid < 0 || n_bid > cap || n_ask < 0 || n_ask > cap;
+    if constexpr (Book::kInRegisters) {
+        SideVec<K> tmp;
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+            const SideVec<K>& v = x == 0 ? bk.template acquire<0>(tmp) : bk.template acquire<1>(tmp);
+            const int n = x == 0 ? n_bid : n_ask;
+            const int32_t nxt = __shfl_down_sync(kFull, v.px[0], 1);
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const int s = l * K + j;
+                const int32_t right = j + 1 < K ? v.px[j + 1] : nxt;
+                if (s < n && v.q[j] <= 0) bad = true;
+                if (s + 1 < n && (x == 0 ? v.px[j] < right : v.px[j] > right)) bad = true;
+            }
+        }
+    } else {
+#pragma unroll 1
+        for (int x = 0; x < 2; ++x) {  // stored worst first: index i+1 ranks ahead of i
+            const GSide<K> sd{bk.template side<0>() + x * Geo<K>::SIDE_BYTES};
+            const int n = x == 0 ? n_bid : n_ask;
+            for (int i = l; i < n && i < 32 * K; i += 32) {
+                if (sd.qty()[i] <= 0) bad = true;
+                if (i + 1 < n && (x == 0 ? sd.px()[i] > sd.px()[i + 1] : sd.px()[i] < sd.px()[i + 1]))
+                    bad = true;
+            }
+        }
+    }
+    if (n_bid > 0 && n_ask > 0 && n_bid <= cap && n_ask <= cap &&
+        bk.template best_px<0>(n_bid) >= bk.template best_px<1>(n_ask))
+        bad = true;
+    if (__any_sync(kFull, bad) && l == 0) atomicOr(status, LOB_STATUS_CHECK);
+#else
+    (void)bk;
+    (void)n_bid;
+    (void)n_ask;
+    (void)cap;
+    (void)status;
+#endif
+}
+
 // Top `depth` price levels of one side whose lane vectors are px/q with n
 // live slots (Sec. 5.1.1 ten-level state): level k = k-th distinct price in
 // priority order with the summed quantity of its orders (saturating at

@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                 }
                 apply_message<K, false>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
                                  hb.z, hb.w, ts, tally, obs, kSnap);
+                check_book<K>(bk, n_bid, n_ask, a.cap, a.status);
                 if constexpr (kTrace) {
                     const int4 top = level1_book<K>(bk, n_bid, n_ask);
                     if (l == 0) reinterpret_cast<int4*>(a.l1)[lo + (int64_t)c * chunk + i] = top;

@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                     }
                     apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
                                      hb.y, hb.z, hb.w, ts, tally, obs, kSnap);
+                    check_book<K>(bk, n_bid, n_ask, a.cap, a.status);
                     if (kTrace && phase == 0) {
                         const int4 top = level1_book<K>(bk, n_bid, n_ask);
                         if (l == 0)
