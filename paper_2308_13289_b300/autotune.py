@@ -18,7 +18,9 @@ from . import Engine, LobError
 CACHE_ENV = "LOB_AUTOTUNE_CACHE"
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune_cache.json")
 
-WARPS = (1, 2, 4, 8, 16)
+# non-powers of two too: with large books, shared memory decides how many
+# warps fit on an SM, and all books resident at once (one wave) is what counts
+WARPS = (1, 2, 3, 4, 6, 7, 8, 16)
 CHUNKS = (32, 64, 128, 256)
 
 
