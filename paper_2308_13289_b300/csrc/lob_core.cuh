@@ -289,18 +289,6 @@ __device__ __forceinline__ void drop_front(T (&v)[K], int m)
     }
 }
 
-// drop_front for a compile-time 0 < M < K: new slot s takes old slot s + M;
-// only the first M values of the next lane cross lanes.
-template <int K, int M, typename T>
-__device__ __forceinline__ void drop_front_small(T (&v)[K])
-{
-    T nxt[M];
-#pragma unroll
-    for (int j = 0; j < M; ++j) nxt[j] = __shfl_down_sync(kFull, v[j], 1);
-#pragma unroll
-    for (int j = 0; j < K; ++j) v[j] = (j + M < K) ? v[j + M] : nxt[j + M - K];
-}
-
 // Does this lane own a slot in [lo, hi)?
 template <int K>
 __device__ __forceinline__ bool lane_touches(int lo, int hi)
@@ -365,15 +353,19 @@ __device__ __forceinline__ bool at_least(int32_t a, int32_t p)
 template <int K>
 struct RegBook {
     SideVec<K> s[2];
+    int32_t bp[2];  // each side's best price (slot 0), warp-uniform; stale while the side is empty
     static constexpr bool kInRegisters = true;
     static constexpr bool kGrouped = false;
     // the side itself is modified in place; `tmp` is unused
     template <int X> __device__ __forceinline__ SideVec<K>& acquire(SideVec<K>&) { return s[X]; }
     template <int X> __device__ __forceinline__ void release(const SideVec<K>&, bool) {}
-    template <int X> __device__ __forceinline__ int32_t best_px(int) const
+    template <int X> __device__ __forceinline__ int32_t best_px(int) const { return bp[X]; }
+    // re-read side X's best price after an operation that may have changed slot 0
+    template <int X> __device__ __forceinline__ void refresh_best()
     {
-        return __shfl_sync(kFull, s[X].px[0], 0);
+        bp[X] = __shfl_sync(kFull, s[X].px[0], 0);
     }
+    template <int X> __device__ __forceinline__ void set_best(int32_t p) { bp[X] = p; }
     // qty of slot p held by lane L at position jj
     template <int X> __device__ __forceinline__ void set_qty(int L, int jj, int p, int32_t q)
     {
@@ -387,6 +379,8 @@ struct RegBook {
     {
         load_side(img, s[0]);
         load_side(img + Geo<K>::SIDE_BYTES, s[1]);
+        refresh_best<0>();
+        refresh_best<1>();
     }
     __device__ __forceinline__ void to_image(char* img) const
     {
@@ -445,6 +439,8 @@ struct SmemBook {
     {
         if (lane_id() == L) reinterpret_cast<int32_t*>(side<X>() + Geo<K>::QTY)[p] = q;
     }
+    template <int X> __device__ __forceinline__ void refresh_best() {}
+    template <int X> __device__ __forceinline__ void set_best(int32_t) {}
     __device__ __forceinline__ void from_image(const char*) {}
     __device__ __forceinline__ void to_image(char*) const {}
 };
@@ -575,6 +571,7 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
     shift_in_prev<K>(v.tlo, p, n_after, tlo, pv_tlo);
     shift_in_prev<K>(v.thi, p, n_after, thi, pv_thi);
     bk.template release<X>(v, lane_touches<K>(p, n_after));
+    if (p == 0) bk.template set_best<X>(P);
     n = n_after;
     ctr.rested += 1;
 }
@@ -634,34 +631,8 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
     shift_out_next<K>(v.tlo, p, n, nx_tlo);
     shift_out_next<K>(v.thi, p, n, nx_thi);
     bk.template release<X>(v, lane_touches<K>(p, n - 1));
+    bk.template refresh_best<X>();
     n -= 1;
-}
-
-// Remove the first m (0 < m < K) slots of every field: a uniform switch over
-// the few possible values keeps every register index static.
-template <int K, int M>
-__device__ __forceinline__ void drop_front_fields(SideVec<K>& v)
-{
-    if constexpr (M > 0 && M < K) {
-        drop_front_small<K, M>(v.px);
-        drop_front_small<K, M>(v.q);
-        drop_front_small<K, M>(v.oid);
-        drop_front_small<K, M>(v.tid);
-        drop_front_small<K, M>(v.tlo);
-        drop_front_small<K, M>(v.thi);
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void drop_front_small_all(SideVec<K>& v, int m)
-{
-    if (m == 1) drop_front_fields<K, 1>(v);
-    else if (m == 2) drop_front_fields<K, 2>(v);
-    else if (m == 3) drop_front_fields<K, 3>(v);
-    else if (m == 4) drop_front_fields<K, 4>(v);
-    else if (m == 5) drop_front_fields<K, 5>(v);
-    else if (m == 6) drop_front_fields<K, 6>(v);
-    else drop_front_fields<K, 7>(v);
 }
 
 // Fill observers: NoObs (plain processing) and VwapObs (execution
@@ -796,17 +767,17 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
 #pragma unroll
     for (int j = 0; j < K; ++j) v.q[j] -= fill[j];
     if (m > 0) {
-        if (m < K && K <= 8) {
-            drop_front_small_all<K>(v, m);
-        } else {
-            drop_front<K>(v.px, m);
-            drop_front<K>(v.q, m);
-            drop_front<K>(v.oid, m);
-            drop_front<K>(v.tid, m);
-            drop_front<K>(v.tlo, m);
-            drop_front<K>(v.thi, m);
-        }
+        // one general drop for every m: per-m variants execute fewer
+        // instructions but enlarge the message loop enough to cost more in
+        // instruction fetch than they save
+        drop_front<K>(v.px, m);
+        drop_front<K>(v.q, m);
+        drop_front<K>(v.oid, m);
+        drop_front<K>(v.tid, m);
+        drop_front<K>(v.tlo, m);
+        drop_front<K>(v.thi, m);
         bk.template release<Y>(v, lane_touches<K>(0, n - m));
+        bk.template refresh_best<Y>();
         n -= m;
     } else if (nf > 0) {
         // only slot 0 was partly filled
@@ -1183,8 +1154,11 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
                                               Tally& ctr, Obs& obs, bool snap)
 {
     if constexpr (!kCompact) {
-        // both best prices, fetched before the dispatch so that their latency
-        // overlaps it (a limit's crossing test needs one of them)
+        // both best prices before the dispatch (a limit's crossing test needs
+        // one): register-resident books keep them in uniform registers,
+        // updated only when an operation changes a side's first slot, so
+        // they cost nothing here; grouped books read them from shared memory,
+        // the load overlapping the dispatch
         const int32_t best_bid = bk.template best_px<0>(n_bid);
         const int32_t best_ask = bk.template best_px<1>(n_ask);
         if (op <= OP_LIMIT_ASK) {
@@ -1416,8 +1390,8 @@ __device__ __forceinline__ int4 level1_book(Book& bk, int n_bid, int n_ask)
         SideVec<K> tmp;
         SideVec<K>& vb = bk.template acquire<0>(tmp);
         SideVec<K>& va = bk.template acquire<1>(tmp);
-        const int32_t bb = __shfl_sync(kFull, vb.px[0], 0);
-        const int32_t ba = __shfl_sync(kFull, va.px[0], 0);
+        const int32_t bb = bk.template best_px<0>(n_bid);
+        const int32_t ba = bk.template best_px<1>(n_ask);
         int64_t lb = 0, la = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {

@@ -287,6 +287,7 @@ __global__ void __launch_bounds__(256, 1) k_env(EnvArgs a)
                             bk.template release<1>(v, lane_touches<K>(p, n_ask - 1));
                             if constexpr (!Book::kInRegisters) __syncwarp();
                             n_ask -= 1;
+                            bk.template refresh_best<1>();
                             tally.cancel_hit += 1;
                             tally.cancelled_qty += q;
                             if (l == 0) c_kind[3] += 1;
