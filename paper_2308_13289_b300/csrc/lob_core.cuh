@@ -445,17 +445,18 @@ struct SmemBook {
     __device__ __forceinline__ void to_image(char*) const {}
 };
 
-// GroupBook: the book stays in shared memory and the add / cancel / match
-// operations walk each lane's slots in groups of four, group g of lane l
-// holding indices g*128 + 4*l + (0..3) ("group-striped": 128-bit accesses of
-// a group are conflict-free), in a loop that is not unrolled, touching only
-// the fields and groups an operation needs.  A side of n orders is stored
-// worst first: the order of priority rank r sits at index n-1-r, so the top
-// of the book -- where adds, cancels and fills mostly happen -- is the end of
-// the array, and an operation moves only the orders above the one it
-// touches; consumed orders leave by shortening the side.  Code size and
-// per-group cost do not grow with K.  Code that reads a grouped side in
-// priority order maps rank r to index n-1-r (storage_index<K>).
+// GroupBook: the book stays in shared memory, each field a plain array of
+// the side's C = 32*K slots.  A side of n orders is stored worst first: the
+// order of priority rank r sits at index n-1-r, so the top of the book --
+// where adds, cancels and fills mostly happen -- is the end of the array, an
+// operation moves only the orders above the one it touches, and consumed
+// orders leave by shortening the side.  Adds and removals move whole orders
+// by one index, lane-parallel (64 orders per pass, consecutive words); the
+// cancel search reads every group of 128 slots at once (lane l: indices
+// g*128 + 4*l + (0..3), 128-bit accesses without bank conflicts); a match
+// walks those groups from the top in a loop that is not unrolled.  Code that
+// reads a grouped side in priority order maps rank r to index n-1-r
+// (storage_index<K>).
 template <int K>
 struct GroupBook : SmemBook<K> {
     static constexpr bool kGrouped = true;
@@ -789,7 +790,8 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
 
 // ------------------------------------------------------- grouped operations
 //
-// GroupBook operations: lane l's group g = slots g*128 + 4*l + (0..3).
+// GroupBook operations.  Where they work on groups, lane l's group g holds
+// slots g*128 + 4*l + (0..3).
 
 __device__ __forceinline__ int4 lds4(const int32_t* a) { return *reinterpret_cast<const int4*>(a); }
 __device__ __forceinline__ void sts4(int32_t* a, int4 v) { *reinterpret_cast<int4*>(a) = v; }
@@ -817,84 +819,73 @@ struct GSide {
     __device__ __forceinline__ int64_t* tm() const { return reinterpret_cast<int64_t*>(b + Geo<K>::TM); }
 };
 
-// One pass over the touched groups moving every field together (the loads of
-// all fields are issued before any shuffle, so their latencies overlap).
+// Whole orders (every field) move by one index, lane-parallel: index i of a
+// side is element i of each field array, so a pass moves 64 consecutive
+// orders (two per lane) with plain 4- and 8-byte accesses (consecutive words:
+// no bank conflicts), loading all of them before the warp synchronises and
+// stores.
+
+// Orders at [lo, hi) move up one (to lo+1 .. hi).  Passes run from the top
+// down, so no pass stores into a range that a later pass still loads.
 template <int K>
-__device__ __forceinline__ void g_shift_in_all(GSide<K> sd, int p, int n_after, int32_t P, int32_t Q,
-                                               int32_t oid, int32_t tid, int64_t tm)
+__device__ __forceinline__ void g_move_up(GSide<K> sd, int lo, int hi)
 {
     const int l = lane_id();
-    int32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    int64_t c4 = 0;
-    const int g0 = p >> 7, g1 = (n_after - 1) >> 7;
 #pragma unroll 1
-    for (int g = g0; g <= g1; ++g) {
-        const int o = g * 128 + 4 * l;
-        const int4 a = lds4(sd.px() + o), b = lds4(sd.qty() + o), c = lds4(sd.oid() + o),
-                   d = lds4(sd.tid() + o);
-        const Q64 e = lds8(sd.tm() + o);
-        const int s = o;
-        const bool t0 = s == p, t1 = s + 1 == p, t2 = s + 2 == p, t3 = s + 3 == p;
-        const bool m0 = s > p && s < n_after, m1 = s + 1 > p && s + 1 < n_after,
-                   m2 = s + 2 > p && s + 2 < n_after, m3 = s + 3 > p && s + 3 < n_after;
-        const bool touch = s + 3 >= p && s < n_after;
-#define LOB_SHIFT_IN(V, VAL, CARRY, T, ST, PTR)                                   \
-        {                                                                         \
-            const T up = __shfl_up_sync(kFull, V.w, 1);                           \
-            const T prev = l == 0 ? CARRY : up;                                   \
-            CARRY = __shfl_sync(kFull, V.w, 31);                                  \
-            auto nv = V;                                                          \
-            nv.x = t0 ? VAL : (m0 ? prev : V.x);                                  \
-            nv.y = t1 ? VAL : (m1 ? V.x : V.y);                                   \
-            nv.z = t2 ? VAL : (m2 ? V.y : V.z);                                   \
-            nv.w = t3 ? VAL : (m3 ? V.z : V.w);                                   \
-            if (touch) ST(PTR + o, nv);                                           \
+    for (int top = hi; top > lo; top -= 64) {
+        const int i0 = top - 1 - l, i1 = top - 33 - l;
+        const bool a0 = i0 >= lo, a1 = i1 >= lo;
+        const int k0 = a0 ? i0 : lo, k1 = a1 ? i1 : lo;
+        const int32_t p0 = sd.px()[k0], q0 = sd.qty()[k0], o0 = sd.oid()[k0], t0 = sd.tid()[k0];
+        const int32_t p1 = sd.px()[k1], q1 = sd.qty()[k1], o1 = sd.oid()[k1], t1 = sd.tid()[k1];
+        const int64_t e0 = sd.tm()[k0], e1 = sd.tm()[k1];
+        __syncwarp();
+        if (a0) {
+            sd.px()[i0 + 1] = p0;
+            sd.qty()[i0 + 1] = q0;
+            sd.oid()[i0 + 1] = o0;
+            sd.tid()[i0 + 1] = t0;
+            sd.tm()[i0 + 1] = e0;
         }
-        LOB_SHIFT_IN(a, P, c0, int32_t, sts4, sd.px())
-        LOB_SHIFT_IN(b, Q, c1, int32_t, sts4, sd.qty())
-        LOB_SHIFT_IN(c, oid, c2, int32_t, sts4, sd.oid())
-        LOB_SHIFT_IN(d, tid, c3, int32_t, sts4, sd.tid())
-        LOB_SHIFT_IN(e, tm, c4, int64_t, sts8, sd.tm())
-#undef LOB_SHIFT_IN
+        if (a1) {
+            sd.px()[i1 + 1] = p1;
+            sd.qty()[i1 + 1] = q1;
+            sd.oid()[i1 + 1] = o1;
+            sd.tid()[i1 + 1] = t1;
+            sd.tm()[i1 + 1] = e1;
+        }
     }
 }
 
+// Orders at [lo, hi) move down one (to lo-1 .. hi-2); passes run from the
+// bottom up.
 template <int K>
-__device__ __forceinline__ void g_shift_out_all(GSide<K> sd, int p, int n)
+__device__ __forceinline__ void g_move_down(GSide<K> sd, int lo, int hi)
 {
     const int l = lane_id();
-    int32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    int64_t c4 = 0;
-    const int last = n - 1;
-    const int g0 = p >> 7, g1 = last >> 7;
 #pragma unroll 1
-    for (int g = g1; g >= g0; --g) {
-        const int o = g * 128 + 4 * l;
-        const int4 a = lds4(sd.px() + o), b = lds4(sd.qty() + o), c = lds4(sd.oid() + o),
-                   d = lds4(sd.tid() + o);
-        const Q64 e = lds8(sd.tm() + o);
-        const int s = o;
-        const bool m0 = s >= p && s < last, m1 = s + 1 >= p && s + 1 < last,
-                   m2 = s + 2 >= p && s + 2 < last, m3 = s + 3 >= p && s + 3 < last;
-        const bool touch = s + 3 >= p && s < last;
-#define LOB_SHIFT_OUT(V, CARRY, T, ST, PTR)                                       \
-        {                                                                         \
-            const T dn = __shfl_down_sync(kFull, V.x, 1);                         \
-            const T next = l == 31 ? CARRY : dn;                                  \
-            CARRY = __shfl_sync(kFull, V.x, 0);                                   \
-            auto nv = V;                                                          \
-            nv.x = m0 ? V.y : V.x;                                                \
-            nv.y = m1 ? V.z : V.y;                                                \
-            nv.z = m2 ? V.w : V.z;                                                \
-            nv.w = m3 ? next : V.w;                                               \
-            if (touch) ST(PTR + o, nv);                                           \
+    for (int bot = lo; bot < hi; bot += 64) {
+        const int i0 = bot + l, i1 = bot + 32 + l;
+        const bool a0 = i0 < hi, a1 = i1 < hi;
+        const int k0 = a0 ? i0 : lo, k1 = a1 ? i1 : lo;
+        const int32_t p0 = sd.px()[k0], q0 = sd.qty()[k0], o0 = sd.oid()[k0], t0 = sd.tid()[k0];
+        const int32_t p1 = sd.px()[k1], q1 = sd.qty()[k1], o1 = sd.oid()[k1], t1 = sd.tid()[k1];
+        const int64_t e0 = sd.tm()[k0], e1 = sd.tm()[k1];
+        __syncwarp();
+        if (a0) {
+            sd.px()[i0 - 1] = p0;
+            sd.qty()[i0 - 1] = q0;
+            sd.oid()[i0 - 1] = o0;
+            sd.tid()[i0 - 1] = t0;
+            sd.tm()[i0 - 1] = e0;
         }
-        LOB_SHIFT_OUT(a, c0, int32_t, sts4, sd.px())
-        LOB_SHIFT_OUT(b, c1, int32_t, sts4, sd.qty())
-        LOB_SHIFT_OUT(c, c2, int32_t, sts4, sd.oid())
-        LOB_SHIFT_OUT(d, c3, int32_t, sts4, sd.tid())
-        LOB_SHIFT_OUT(e, c4, int64_t, sts8, sd.tm())
-#undef LOB_SHIFT_OUT
+        if (a1) {
+            sd.px()[i1 - 1] = p1;
+            sd.qty()[i1 - 1] = q1;
+            sd.oid()[i1 - 1] = o1;
+            sd.tid()[i1 - 1] = t1;
+            sd.tm()[i1 - 1] = e1;
+        }
     }
 }
 
@@ -905,18 +896,18 @@ __device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rul
 {
     const GSide<K> sd{side};
     const int l = lane_id();
-    // p = orders at least as good as P: the top p indices n-p .. n-1; count
-    // group by group from the top until a group holds one that is not
+    // p = orders at least as good as P, the top p indices n-p .. n-1: lane l
+    // looks at priority ranks l and l+32 of a 64-order window from the top;
+    // the side is sorted, so the ranks that hold such an order are a prefix
     int p = 0;
 #pragma unroll 1
-    for (int g = (n - 1) >> 7; g >= 0; --g) {
-        const int s = g * 128 + 4 * l;
-        const int4 v = lds4(sd.px() + s);
-        const int c = (s < n && at_least<X>(v.x, P)) + (s + 1 < n && at_least<X>(v.y, P)) +
-                      (s + 2 < n && at_least<X>(v.z, P)) + (s + 3 < n && at_least<X>(v.w, P));
-        const int gc = (int)__reduce_add_sync(kFull, (unsigned)c);
-        p += gc;
-        if (gc < min(128, n - g * 128)) break;
+    for (int top = n; top > 0; top -= 64) {
+        const int i0 = top - 1 - l, i1 = top - 33 - l;
+        const bool ok0 = i0 >= 0 && at_least<X>(sd.px()[i0 >= 0 ? i0 : 0], P);
+        const bool ok1 = i1 >= 0 && at_least<X>(sd.px()[i1 >= 0 ? i1 : 0], P);
+        const int c = __popc(__ballot_sync(kFull, ok0)) + __popc(__ballot_sync(kFull, ok1));
+        p += c;
+        if (c < 64) break;
     }
     const bool full = n >= cap;
     if (full && (rule != 0 || p >= cap)) {
@@ -929,13 +920,20 @@ __device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rul
         // every other order moves down one
         ctr.evicted += 1;
         ctr.evicted_qty += sd.qty()[0];
-        g_shift_out_all<K>(sd, 0, n);
+        g_move_down<K>(sd, 1, n);
         n -= 1;
         __syncwarp();
     }
     // the new order goes below the p orders at least as good, which move up
-    const int64_t tm = (int64_t)(((uint64_t)(uint32_t)thi << 32) | (uint32_t)tlo);
-    g_shift_in_all<K>(sd, n - p, n + 1, P, Q, oid, tid, tm);
+    const int lo = n - p;
+    g_move_up<K>(sd, lo, n);
+    if (l == 0) {
+        sd.px()[lo] = P;
+        sd.qty()[lo] = Q;
+        sd.oid()[lo] = oid;
+        sd.tid()[lo] = tid;
+        sd.tm()[lo] = (int64_t)(((uint64_t)(uint32_t)thi << 32) | (uint32_t)tlo);
+    }
     n += 1;
     ctr.rested += 1;
 }
@@ -972,22 +970,20 @@ __device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, 
 {
     const GSide<K> sd{side};
     const int l = lane_id();
-    int p = -1;
-#pragma unroll 1
-    for (int g = (n - 1) >> 7; g >= 0; --g) {  // recent orders sit near the top
-        const int4 v = lds4(sd.oid() + g * 128 + 4 * l);
+    // every group at once (independent loads) and one warp maximum: live ids
+    // are unique on a side, so at most one slot matches
+    int mine = -1;
+#pragma unroll
+    for (int g = 0; g < K / 4; ++g) {
         const int s = g * 128 + 4 * l;
-        int jj = (s + 3 < n && v.w == oid) ? 3 : -1;
-        jj = (s + 2 < n && v.z == oid) ? 2 : jj;
-        jj = (s + 1 < n && v.y == oid) ? 1 : jj;
-        jj = (s < n && v.x == oid) ? 0 : jj;
-        const unsigned hit = __ballot_sync(kFull, jj >= 0);
-        if (hit) {
-            const int L = __ffs(hit) - 1;
-            p = g * 128 + 4 * L + __shfl_sync(kFull, jj, L);
-            break;
-        }
+        const int4 v = lds4(sd.oid() + s);
+        int mg = (s < n && v.x == oid) ? s : -1;
+        mg = (s + 1 < n && v.y == oid) ? s + 1 : mg;
+        mg = (s + 2 < n && v.z == oid) ? s + 2 : mg;
+        mg = (s + 3 < n && v.w == oid) ? s + 3 : mg;
+        mine = max(mine, mg);
     }
+    int p = __reduce_max_sync(kFull, mine);
     if (p < 0 && snap) p = g_find_snapshot<K>(side, n, P);
     if (p < 0) return;
     ctr.cancel_hit += 1;
@@ -1000,7 +996,8 @@ __device__ __forceinline__ void g_cancel_order(char* side, int& n, int32_t oid, 
         return;
     }
     ctr.cancelled_qty += q_old;
-    g_shift_out_all<K>(sd, p, n);  // the orders above move down one
+    __syncwarp();
+    g_move_down<K>(sd, p + 1, n);  // the orders above move down one
     n -= 1;
 }
 
@@ -1013,6 +1010,33 @@ __device__ __forceinline__ int32_t g_match_order(char* side, int& n, int32_t P, 
     // groups from the top, lanes from 31 down, and w, z, y, x inside a lane.
     const GSide<K> sd{side};
     const int l = lane_id();
+    // Every caller has checked that the side is not empty and that its best
+    // order crosses.  When that order alone fills the aggressor (Q <= its
+    // quantity) the loop runs once: one trade, written by lane 0, no scan.
+    {
+        const int top = n - 1;
+        const int32_t q_top = sd.qty()[top];
+        if (Q <= q_top) {
+            const int32_t px_top = sd.px()[top], tid_top = sd.tid()[top];
+            if (l == 0) {
+                if (ts.count < (int64_t)ts.cap) {
+                    int4* dst = reinterpret_cast<int4*>(ts.log + ts.count);
+                    dst[0] = make_int4(px_top, Q, oid_a, sd.oid()[top]);
+                    dst[1] = make_int4(tid_a, tid_top, tlo, thi);
+                }
+                if (Q < q_top) sd.qty()[top] = q_top - Q;
+            }
+            const int32_t fill[4] = {l == 0 ? Q : 0, 0, 0, 0};
+            const int32_t pa[4] = {px_top, px_top, px_top, px_top};
+            const int32_t ta[4] = {tid_top, tid_top, tid_top, tid_top};
+            obs.template on_fills<4>(fill, pa, ta, tid_a);
+            ts.count += 1;
+            ctr.traded_qty += Q;
+            if (Q == q_top) n -= 1;  // used up: it was the top of the side
+            __syncwarp();
+            return 0;
+        }
+    }
     const int n0 = n;
     const int g_top = (n0 - 1) >> 7;
     uint32_t consumed = 0;  // quantity filled so far (warp-uniform)
