@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--oracle-books", type=int, default=256,
                     help="books of the CPU-baseline sample (full streams)")
     ap.add_argument("--launch", default="", help="warps,chunk,ctas_per_sm override")
+    ap.add_argument("--capacity", type=int, default=0,
+                    help="book capacity override for the replay workloads (1..512)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uneven / RL-environment / serving workloads")
     ap.add_argument("--serving-window", type=float, default=2.0,
@@ -192,7 +194,7 @@ def run_engine(args):
     w, params, counts, msgs, off, sid = workload_streams(args.workload, rank)
     n = len(counts)
     total_msgs = int(off[-1])
-    cap = w["capacity"]
+    cap = args.capacity or w["capacity"]
     tcap = trade_capacity_for(counts)
     depth = 10
 
@@ -369,9 +371,11 @@ def run_engine(args):
     state_bytes = 2 * n * eng_book_bytes(cap)
     alg_bytes = 32 * total_msgs + 32 * trades_per_step + state_bytes + 8 * (n + 1)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = measured_traffic() if args.workload == "replay_1024x100k" else None
+    traffic = (measured_traffic() if args.workload == "replay_1024x100k" and cap == 100
+               else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 5), "traffic": traffic, "kernel": "k_process<4>",
+            "frac": round(achieved / peak, 5), "traffic": traffic,
+            "kernel": "k_process<%d>" % (eng_book_bytes(cap) // (48 * 32)),
             "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": int(alg_bytes),
             "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
 
@@ -885,7 +889,7 @@ def run_reference(args):
     n_sample = min(64, len(counts))
     sub_off = off[:n_sample + 1]
     sub = msgs[:int(sub_off[-1])]
-    cap, tcap = w["capacity"], trade_capacity_for(counts)
+    cap, tcap = args.capacity or w["capacity"], trade_capacity_for(counts)
     threads = oracle.default_threads()
     n_msgs = int(sub_off[-1])
 
