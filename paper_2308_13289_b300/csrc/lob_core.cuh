@@ -680,7 +680,7 @@ struct TradeSink {
 // slot s therefore receives min(Q_s, max(0, Q - (quantity of slots before s))),
 // which one saturating warp prefix scan gives for all slots at once.
 // Returns the aggressor's remaining quantity max(0, Q_a).
-template <int K, int Y, bool kFast = false, class Book, class Obs>
+template <int K, int Y, class Book, class Obs>
 __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int32_t Q, int32_t oid_a,
                                                int32_t tid_a, int32_t tlo, int32_t thi,
                                                TradeSink& ts, Tally& ctr, Obs& obs)
@@ -691,41 +691,38 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
     const int l = lane_id();
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<Y>(tmp);
-    if constexpr (kFast) {
-        // Every caller has checked that the side is not empty and that its
-        // best order crosses.  When that order alone fills the aggressor
-        // (Q <= its quantity) the loop runs once: one trade, written by lane
-        // 0, which holds the order, and no scan.  Compiled into the message
-        // loop whose timing it was measured in (the full dispatch); the
-        // compact dispatch of the environment kernel keeps the scan only.
-        const int32_t q0 = __shfl_sync(kFull, v.q[0], 0);
-        if (Q <= q0) {
-            if (l == 0 && ts.count < (int64_t)ts.cap) {
-                int4* dst = reinterpret_cast<int4*>(ts.log + ts.count);
-                dst[0] = make_int4(v.px[0], Q, oid_a, v.oid[0]);
-                dst[1] = make_int4(tid_a, v.tid[0], tlo, thi);
-            }
-            int32_t fill[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) fill[j] = (l == 0 && j == 0) ? Q : 0;
-            obs.template on_fills<K>(fill, v.px, v.tid, tid_a);
-            ts.count += 1;
-            ctr.traded_qty += Q;
-            if (Q == q0) {
-                drop_front<K>(v.px, 1);
-                drop_front<K>(v.q, 1);
-                drop_front<K>(v.oid, 1);
-                drop_front<K>(v.tid, 1);
-                drop_front<K>(v.tlo, 1);
-                drop_front<K>(v.thi, 1);
-                bk.template release<Y>(v, lane_touches<K>(0, n - 1));
-                bk.template refresh_best<Y>();
-                n -= 1;
-            } else {
-                bk.template set_qty<Y>(0, 0, 0, q0 - Q);
-            }
-            return 0;
+
+    // Every caller has checked that the side is not empty and that its best
+    // order crosses.  When that order alone fills the aggressor (Q <= its
+    // quantity) the loop runs once: one trade, written by lane 0, which holds
+    // the order, and no scan.
+    const int32_t q0 = __shfl_sync(kFull, v.q[0], 0);
+    if (Q <= q0) {
+        if (l == 0 && ts.count < (int64_t)ts.cap) {
+            int4* dst = reinterpret_cast<int4*>(ts.log + ts.count);
+            dst[0] = make_int4(v.px[0], Q, oid_a, v.oid[0]);
+            dst[1] = make_int4(tid_a, v.tid[0], tlo, thi);
         }
+        int32_t fill[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) fill[j] = (l == 0 && j == 0) ? Q : 0;
+        obs.template on_fills<K>(fill, v.px, v.tid, tid_a);
+        ts.count += 1;
+        ctr.traded_qty += Q;
+        if (Q == q0) {
+            drop_front<K>(v.px, 1);
+            drop_front<K>(v.q, 1);
+            drop_front<K>(v.oid, 1);
+            drop_front<K>(v.tid, 1);
+            drop_front<K>(v.tlo, 1);
+            drop_front<K>(v.thi, 1);
+            bk.template release<Y>(v, lane_touches<K>(0, n - 1));
+            bk.template refresh_best<Y>();
+            n -= 1;
+        } else {
+            bk.template set_qty<Y>(0, 0, 0, q0 - Q);
+        }
+        return 0;
     }
 
     // crossing quantity per slot and lane-local inclusive prefix
@@ -1225,12 +1222,12 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
             if (op == OP_LIMIT_BID) {  // buy limit: match the asks, then rest the remainder as a bid
                 int32_t rest = Q;
                 if (n_ask > 0 && at_least<1>(best_ask, P))
-                    rest = match_order<K, 1, true>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                    rest = match_order<K, 1>(bk, n_ask, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
                 if (rest > 0) add_order<K, 0>(bk, n_bid, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
             } else if (op == OP_LIMIT_ASK) {
                 int32_t rest = Q;
                 if (n_bid > 0 && at_least<0>(best_bid, P))
-                    rest = match_order<K, 0, true>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                    rest = match_order<K, 0>(bk, n_bid, P, rest, oid, tid, tlo, thi, ts, ctr, obs);
                 if (rest > 0) add_order<K, 1>(bk, n_ask, cap, rule, P, rest, oid, tid, tlo, thi, ctr);
             }
         } else if (op <= OP_CANCEL_ASK) {  // cancel and delete are treated identically
@@ -1241,9 +1238,9 @@ __device__ __forceinline__ void apply_message(Book& bk, int& n_bid, int& n_ask, 
         } else {  // market: price max_int (buy) / 0 (sell), remainder dropped
             int32_t rest = Q;
             if (op == OP_MARKET_BID) {
-                if (n_ask > 0) rest = match_order<K, 1, true>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                if (n_ask > 0) rest = match_order<K, 1>(bk, n_ask, kMaxInt, rest, oid, tid, tlo, thi, ts, ctr, obs);
             } else {
-                if (n_bid > 0) rest = match_order<K, 0, true>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr, obs);
+                if (n_bid > 0) rest = match_order<K, 0>(bk, n_bid, 0, rest, oid, tid, tlo, thi, ts, ctr, obs);
             }
             ctr.discarded_qty += rest;
         }
