@@ -735,29 +735,18 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
         acc = sat_add(acc, cq[j]);
         loc[j] = acc;
     }
-    // When the fills end inside lane 0's slots (lane 0 alone covers Q, or the
-    // crossing prefix does not reach lane 1) no warp-wide scan is needed.
-    const unsigned first_crosses = __ballot_sync(kFull, cq[0] != 0u);
-    const uint32_t acc0 = __shfl_sync(kFull, acc, 0);
-    const bool local = acc0 >= (uint32_t)Q || !(first_crosses & 2u);
-    uint32_t excl, total;
-    if (local) {
-        excl = l == 0 ? 0u : (uint32_t)Q;  // lanes other than 0 get no room
-        total = acc0;
-    } else {
-        // warp inclusive scan of the lane totals (saturating at INT32_MAX:
-        // exact wherever the running total is below Q <= INT32_MAX, which is
-        // all that the fills depend on)
-        uint32_t incl = acc;
+    // warp inclusive scan of the lane totals (saturating at INT32_MAX: exact
+    // wherever the running total is below Q <= INT32_MAX, which is all that
+    // the fills depend on)
+    uint32_t incl = acc;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(kFull, incl, d);
-            if (l >= d) incl = sat_add(incl, t);
-        }
-        excl = __shfl_up_sync(kFull, incl, 1);
-        if (l == 0) excl = 0;
-        total = __shfl_sync(kFull, incl, 31);
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, d);
+        if (l >= d) incl = sat_add(incl, t);
     }
+    uint32_t excl = __shfl_up_sync(kFull, incl, 1);
+    if (l == 0) excl = 0;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
 
     int32_t fill[K];
     unsigned nfull = 0, nfill = 0;
@@ -769,15 +758,9 @@ __device__ __forceinline__ int32_t match_order(Book& bk, int& n, int32_t P, int3
         nfull += (cq[j] != 0u && (uint32_t)fill[j] == cq[j]) ? 1u : 0u;
         nfill += fill[j] > 0 ? 1u : 0u;
     }
-    int m, nf;  // fully filled orders (they leave the book), trades of this message
-    if (local) {
-        const unsigned packed = __shfl_sync(kFull, nfull | (nfill << 16), 0);
-        m = (int)(packed & 0xffffu);
-        nf = (int)(packed >> 16);
-    } else {
-        m = (int)__reduce_add_sync(kFull, nfull);
-        nf = (int)__reduce_add_sync(kFull, nfill);
-    }
+    // fully filled orders (they leave the book), trades of this message
+    const int m = (int)__reduce_add_sync(kFull, nfull);
+    const int nf = (int)__reduce_add_sync(kFull, nfill);
     const int32_t F = (int32_t)min(total, (uint32_t)Q);  // quantity traded
 
     // trades: the filled slots are the prefix [0, nf), trade k -> slot k
