@@ -1438,13 +1438,14 @@ __device__ __forceinline__ int4 level1_book(Book& bk, int n_bid, int n_ask)
             lb += (l * K + j < n_bid && vb.px[j] == bb) ? vb.q[j] : 0;
             la += (l * K + j < n_ask && va.px[j] == ba) ? va.q[j] : 0;
         }
-        if (!__any_sync(kFull, ((lb | la) >> 27) != 0)) {  // 32 parts < 2^27: no overflow
-            qb = __reduce_add_sync(kFull, (unsigned)lb);
-            qa = __reduce_add_sync(kFull, (unsigned)la);
-        } else {
-            qb = warp_sum64(lb);
-            qa = warp_sum64(la);
-        }
+        // a lane's part is below 2^33 (K <= 4 quantities < 2^31): its 16-bit
+        // low and high halves sum over 32 lanes without overflow, exactly
+        const unsigned b_lo = __reduce_add_sync(kFull, (unsigned)(lb & 0xffff));
+        const unsigned b_hi = __reduce_add_sync(kFull, (unsigned)(lb >> 16));
+        const unsigned a_lo = __reduce_add_sync(kFull, (unsigned)(la & 0xffff));
+        const unsigned a_hi = __reduce_add_sync(kFull, (unsigned)(la >> 16));
+        qb = ((int64_t)b_hi << 16) + b_lo;
+        qa = ((int64_t)a_hi << 16) + a_lo;
         pb = n_bid > 0 ? bb : -1;
         pa = n_ask > 0 ? ba : -1;
     }
