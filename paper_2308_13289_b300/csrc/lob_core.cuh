@@ -674,9 +674,10 @@ struct TradeSink {
 
 // Matching (Sec. 4.1 item 3 and its while loop) of an aggressor of quantity Q
 // with limit price P (0 / max_int for market orders, Sec. 4.2 item 3) against
-// opposite side Y.  The loop "take Best(o_s), apply Q_s' = max(0, Q_s - Q_a),
-// Q_a' = Q_a - Q_s, log t = [P_s, Q_s - Q_s', OID_a, OID_s, time_a]" visits the
-// crossing prefix of the priority-sorted side in order; the standing order at
+// opposite side Y.  The method's loop repeatedly takes the best standing
+// order, reduces it to max(0, Q_s - Q_a), reduces the aggressor by Q_s and
+// logs the trade [P_s, filled quantity, OID_a, OID_s, time_a]; it therefore
+// visits the crossing prefix of the priority-sorted side in order: the order at
 // slot s therefore receives min(Q_s, max(0, Q - (quantity of slots before s))),
 // which one saturating warp prefix scan gives for all slots at once.
 // Returns the aggressor's remaining quantity max(0, Q_a).
