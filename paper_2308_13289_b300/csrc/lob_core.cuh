@@ -609,14 +609,6 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
     const int32_t q_mine = pick<K>(v.q, jj < 0 ? 0 : jj);
     const int j_hit = __shfl_sync(kFull, jj, L);
     const int32_t q_old = __shfl_sync(kFull, q_mine, L);
-    // a removal's cross-lane values, fetched alongside (unused when the order
-    // stays)
-    const int32_t nx_px = __shfl_down_sync(kFull, v.px[0], 1);
-    const int32_t nx_q = __shfl_down_sync(kFull, v.q[0], 1);
-    const int32_t nx_oid = __shfl_down_sync(kFull, v.oid[0], 1);
-    const int32_t nx_tid = __shfl_down_sync(kFull, v.tid[0], 1);
-    const int32_t nx_tlo = __shfl_down_sync(kFull, v.tlo[0], 1);
-    const int32_t nx_thi = __shfl_down_sync(kFull, v.thi[0], 1);
     const int p = L * K + j_hit;
     const int32_t q_new = q_old - Q;
     if (q_new > 0) {
@@ -625,6 +617,14 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
         return;
     }
     ctr.cancelled_qty += q_old;
+    // the removal's cross-lane values (fetched only now: partial cancels and
+    // misses, 29 % of the message mix, never need them)
+    const int32_t nx_px = __shfl_down_sync(kFull, v.px[0], 1);
+    const int32_t nx_q = __shfl_down_sync(kFull, v.q[0], 1);
+    const int32_t nx_oid = __shfl_down_sync(kFull, v.oid[0], 1);
+    const int32_t nx_tid = __shfl_down_sync(kFull, v.tid[0], 1);
+    const int32_t nx_tlo = __shfl_down_sync(kFull, v.tlo[0], 1);
+    const int32_t nx_thi = __shfl_down_sync(kFull, v.thi[0], 1);
     shift_out_next<K>(v.px, p, n, nx_px);
     shift_out_next<K>(v.q, p, n, nx_q);
     shift_out_next<K>(v.oid, p, n, nx_oid);
