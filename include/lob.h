@@ -108,7 +108,8 @@ enum {
     LOB_STATUS_TIMEOUT = 1,       /* a message chunk did not arrive within the wait bound */
     LOB_STATUS_BAD_BOOK = 2,      /* a book id outside [0, n_books) was skipped            */
     LOB_STATUS_BAD_SEGMENT = 4,   /* a segment with offsets[i+1] < offsets[i] was skipped  */
-    LOB_STATUS_BAD_BOOK_LOAD = 8, /* lob_set_book: a side not in priority order was emptied */
+    LOB_STATUS_BAD_BOOK_LOAD = 8, /* lob_set_book / lob_init_from_levels: a side not in
+                                     priority order was loaded empty                      */
     LOB_STATUS_CHECK = 16         /* checked builds only (-DLOB_CHECKS): after some message a
                                      book broke an invariant (side count outside 0..capacity,
                                      a side out of priority order, a resting quantity <= 0,
@@ -255,6 +256,30 @@ int lob_set_book(lob_ctx* ctx, const int32_t* d_price, const int32_t* d_qty,
                  const int32_t* d_oid, const int32_t* d_tid, const int64_t* d_time,
                  const int32_t* d_count, void* stream);
 
+/* Initialise every book from a level snapshot (Sec. 5.1.1: an episode starts
+ * from the book's first levels, each known only by its price and total
+ * volume, so each level enters the book as ONE order holding that volume,
+ * with OIDs from -9000 downward).
+ *   d_bid_px, d_bid_qty, d_ask_px, d_ask_qty: int32[n_books][depth] (device),
+ *     level k = the k-th best price of the side and its volume -- the layout
+ *     lob_get_levels writes.  A side's listed levels are those before its
+ *     first level with price <= 0 or volume <= 0 (a shorter side ends there).
+ *   depth: 1..capacity.
+ *   time_ns: the time stamp every snapshot order carries.
+ * Per book, both sides are replaced: listed level k of a side becomes the
+ * order [price, volume, OID, TID 0, time_ns] at priority rank k; OIDs are
+ * handed out over the listed bid levels best first (-9000, -9001, ...), then
+ * over the listed ask levels best first.  A side whose listed levels are not
+ * in priority order (a bid level priced above the one before it, an ask level
+ * below it) is loaded empty and LOB_STATUS_BAD_BOOK_LOAD is set; its levels
+ * still use up their OIDs.  Trade logs and counters are left as they are.
+ * Combine with LOB_FLAG_SNAPSHOT_CANCELS so that cancels of orders placed
+ * before the snapshot apply to these orders by price.
+ * Errors: LOB_E_INVAL (null pointer, depth outside 1..capacity), LOB_E_CUDA. */
+int lob_init_from_levels(lob_ctx* ctx, const int32_t* d_bid_px, const int32_t* d_bid_qty,
+                         const int32_t* d_ask_px, const int32_t* d_ask_qty, int32_t depth,
+                         int64_t time_ns, void* stream);
+
 /* Counters int64[n_books][LOB_N_COUNTERS] (cumulative since create/reset) and
  * the status word (int32, LOB_STATUS_* bits).  Either pointer may be NULL. */
 int lob_get_stats(lob_ctx* ctx, int64_t* d_counters, int32_t* d_status, void* stream);
@@ -399,14 +424,17 @@ int lob_literal_process(const lob_msg_t* d_msgs, const int64_t* d_offsets, int32
  * (same kernel, same results).  Outputs (caller-owned device memory):
  *   d_trades       lob_trade_t[n_books][trade_capacity]: trades in execution
  *                  order; entries past a book's count are left untouched
- *   d_trade_counts int64[n_books]: trades executed per book
+ *   d_trade_counts int64[n_books]: trades executed per book (zeroed first, so
+ *                  a book skipped with LOB_STATUS_BAD_SEGMENT reads 0)
  *   d_counters     int64[n_books][LOB_N_COUNTERS] (overwritten, not accumulated)
  *   d_price .. d_count: final canonical book as in lob_get_book (each may be NULL)
  *   d_status       int32 status word (LOB_STATUS_*), overwritten
- * Limits: capacity 1..512; the scratch must hold n_books books, about
- * 32 MiB / (48 * roundup(capacity, 32) + 8) books (5,460 at capacity 100,
- * 1,365 at capacity 512); larger requests return LOB_E_INVAL with the limit in
- * lob_last_error().  The first call on a device resolves the array's device
+ * Limits: capacity 1..512; the scratch must hold n_books books: exactly,
+ *   256 + roundup(8 * n_books, 256) + n_books * B <= 32 MiB (33,554,432 B),
+ * with B = 48 * S bytes per book and S = capacity rounded up to 32, 64, 128,
+ * 256 or 512 slots -- at most 5,454 books at capacity 100 (B = 6,144) and
+ * 1,364 at capacity 512 (B = 24,576).  Larger requests return LOB_E_INVAL
+ * with the limit in lob_last_error().  The first call on a device resolves the array's device
  * address and sets kernel attributes for that device; make that first call
  * before any stream capture.  Every call reuses the same array: calls whose
  * work overlaps on the GPU (different streams, or several host threads) race
@@ -434,7 +462,6 @@ int64_t lob_launch_count(const lob_ctx* ctx);
 /* Human-readable description of the calling thread's most recent error. */
 const char* lob_last_error(void);
 
-/* Library ABI version (incremented on incompatible change). */
 /* Failure handling self-test (no counterpart in the paper): run the bounded
  * wait that guards every staged copy on an mbarrier that nothing completes,
  * for limit_ns (1 ns .. 1 s).  The wait gives up as designed, OR-s
@@ -443,6 +470,7 @@ const char* lob_last_error(void);
  * hang: the device stays usable.  LOB_E_INVAL on a bad argument. */
 int lob_selftest_wait(int64_t limit_ns, int32_t* d_status, uint64_t* d_elapsed_ns, void* stream);
 
+/* Library ABI version (incremented on incompatible change). */
 int lob_abi_version(void);
 
 #ifdef __cplusplus

@@ -100,6 +100,8 @@ def _oracle_lib():
     lib.oracle_get_trades.argtypes = [vp, vp, vp]
     lib.oracle_get_book.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.oracle_set_book.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+    lib.oracle_init_from_levels.restype = i32
+    lib.oracle_init_from_levels.argtypes = [vp, vp, vp, vp, vp, i32, ctypes.c_int64]
     lib.oracle_get_levels.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.oracle_get_counters.argtypes = [vp, vp]
     lib.oracle_get_resting_qty.argtypes = [vp, vp]
@@ -187,6 +189,17 @@ class Oracle:
                                       _p(a["tid"]), _p(a["time_ns"]), _p(a["count"]))
         if rc != 0:
             raise ValueError("book not in priority order or over capacity")
+
+    def init_from_levels(self, bid_px, bid_qty, ask_px, ask_qty, time_ns=0):
+        """Every book from a level snapshot (Sec. 5.1.1): one order per listed
+        level, OIDs -9000, -9001, ... (bids best first, then asks); inputs
+        int32 [n_books][depth].  Returns the number of sides left empty
+        because their levels were out of priority order or over capacity."""
+        a = [np.ascontiguousarray(x, dtype=np.int32) for x in (bid_px, bid_qty, ask_px, ask_qty)]
+        if any(x.shape != a[0].shape or x.ndim != 2 or x.shape[0] != self.n_books for x in a):
+            raise ValueError("level arrays must all be [n_books][depth]")
+        return int(self.lib.oracle_init_from_levels(self.h, *[_p(x) for x in a], a[0].shape[1],
+                                                    int(time_ns)))
 
     def levels(self, depth: int):
         shp = (self.n_books, depth)

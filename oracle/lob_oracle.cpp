@@ -538,6 +538,57 @@ int oracle_set_book(void* h, const int32_t* px, const int32_t* qty, const int32_
     return 0;
 }
 
+// Initialise every book from a level snapshot (Sec. 5.1.1: the environment
+// starts from the limit order book's snapshot of its first levels; a snapshot
+// knows only each level's price and total volume, so every level enters the
+// book as ONE order holding that volume, with OIDs counting down from -9000).
+// Inputs are [n_books][depth] per array, level k = k-th best price of a side.
+// Per book:
+//   1. the book is emptied;
+//   2. the listed levels of a side are the levels before the first one whose
+//      price or volume is <= 0 (a shorter snapshot ends there);
+//   3. OIDs are handed out in this order: the listed bid levels best first
+//      (-9000, -9001, ...), then the listed ask levels best first;
+//   4. each listed level becomes an order [P = price, Q = volume, OID, TID 0,
+//      time = time_ns], appended in listed order (so equal prices keep the
+//      listing as their arrival order);
+//   5. a side whose listed levels are not in priority order (a bid level above
+//      the one before it, an ask level below it), or that lists more levels
+//      than the capacity, is left empty.
+// Trade logs and counters are not touched.  Returns the number of sides left
+// empty by rule 5.
+int32_t oracle_init_from_levels(void* h, const int32_t* bid_px, const int32_t* bid_qty,
+                                const int32_t* ask_px, const int32_t* ask_qty, int32_t depth,
+                                int64_t time_ns)
+{
+    Engine& E = *(Engine*)h;
+    int32_t rejected = 0;
+    for (int32_t b = 0; b < E.n_books; ++b) {
+        Book& bk = E.books[(size_t)b];
+        bk.bids = Side(true);
+        bk.asks = Side(false);
+        int32_t next_oid = -9000;
+        for (int s = 0; s < 2; ++s) {
+            const int32_t* px = (s == 0 ? bid_px : ask_px) + (int64_t)b * depth;
+            const int32_t* qty = (s == 0 ? bid_qty : ask_qty) + (int64_t)b * depth;
+            Side& sd = s == 0 ? bk.bids : bk.asks;
+            int32_t listed = 0;
+            while (listed < depth && px[listed] > 0 && qty[listed] > 0) ++listed;
+            std::vector<Order> orders;
+            for (int32_t k = 0; k < listed; ++k) orders.push_back(Order{px[k], qty[k], next_oid--, 0, time_ns});
+            bool ok = listed <= E.capacity;
+            for (int32_t k = 1; k < listed; ++k)
+                if (sd.strictly_better(px[k], px[k - 1])) ok = false;
+            if (!ok) {
+                ++rejected;
+                continue;
+            }
+            for (const Order& o : orders) sd.append(o);
+        }
+    }
+    return rejected;
+}
+
 // Top `depth` price levels per side: aggregated quantity per distinct price,
 // best first; empty levels are (-1, 0).  Quantities saturate at max_int.
 static void book_levels(Book& bk, int32_t b, int32_t depth, int32_t* bid_px, int32_t* bid_qty,

@@ -21,7 +21,6 @@ from ._abi import LobConfig, LobEnvConfig, LobError, check
 OVERFLOW_EVICT, OVERFLOW_REJECT = 0, 1
 FLAG_APPEND_TRADES = 1
 FLAG_SNAPSHOT_CANCELS = 2
-SNAPSHOT_OID_START = -9000  # snapshot orders: OIDs -9000, -9001, ... (Sec. 5.1.1)
 N_COUNTERS = 20
 COUNTERS = ["msgs", "limit", "cancel", "market", "noop", "invalid", "trades", "traded_qty",
             "rested", "rejected", "rejected_qty", "evicted", "evicted_qty", "cancel_hit",
@@ -154,6 +153,16 @@ def lob_set_book(h, px, qty, oid, tid, tm, count, stream=None):
                              _ptr(count), _stream(stream)), "lob_set_book")
 
 
+def lob_init_from_levels(h, bid_px, bid_qty, ask_px, ask_qty, time_ns=0, stream=None):
+    depth = bid_px.shape[-1]
+    for t in (bid_qty, ask_px, ask_qty):
+        if t.shape != bid_px.shape or t.dtype != torch.int32:
+            raise ValueError("level arrays must be int32 tensors of one shape [n_books, depth]")
+    check(lib().lob_init_from_levels(h, _ptr(bid_px), _ptr(bid_qty), _ptr(ask_px), _ptr(ask_qty),
+                                     int(depth), int(time_ns), _stream(stream)),
+          "lob_init_from_levels")
+
+
 def lob_get_stats(h, counters, status, stream=None):
     check(lib().lob_get_stats(h, _ptr(counters), _ptr(status), _stream(stream)), "lob_get_stats")
 
@@ -245,39 +254,6 @@ def literal_process(msgs, offsets, capacity, trade_capacity, overflow_rule=OVERF
 
 # ------------------------------------------------------------------ convenience object
 
-def snapshot_books(bid_px, bid_qty, ask_px, ask_qty, capacity, time_ns=0):
-    """Books in the lob_set_book layout built from level snapshots (Sec. 5.1.1):
-    one order per listed level holding the level's whole volume, OIDs -9000,
-    -9001, ... (the bid levels best first, then the ask levels best first),
-    trader id 0, time `time_ns`.  Inputs are int32 [n_books][depth] tensors in
-    the lob_get_levels layout; a level with price <= 0 or quantity <= 0 ends
-    that side.  Returns the dict Engine.set_book takes, on the inputs' device."""
-    sides = [(bid_px, bid_qty), (ask_px, ask_qty)]
-    n, depth = bid_px.shape
-    dev = bid_px.device
-    if capacity < depth:
-        raise ValueError("capacity %d below the snapshot depth %d" % (capacity, depth))
-    shape = (n, 2, capacity)
-    out = {k: torch.full(shape, -1, dtype=torch.int32, device=dev)
-           for k in ("price", "qty", "oid", "tid")}
-    out["time_ns"] = torch.full(shape, -1, dtype=torch.int64, device=dev)
-    out["count"] = torch.zeros((n, 2), dtype=torch.int32, device=dev)
-    base = torch.zeros(n, dtype=torch.int64, device=dev)
-    for s, (px, q) in enumerate(sides):
-        ok = (px > 0) & (q > 0)
-        cnt = torch.cumprod(ok.to(torch.int32), dim=1).sum(dim=1)  # listed levels, in order
-        live = torch.arange(depth, device=dev).unsqueeze(0) < cnt.unsqueeze(1)
-        oid = SNAPSHOT_OID_START - (base.unsqueeze(1) + torch.arange(depth, device=dev))
-        out["price"][:, s, :depth] = torch.where(live, px, -1)
-        out["qty"][:, s, :depth] = torch.where(live, q, -1)
-        out["oid"][:, s, :depth] = torch.where(live, oid.to(torch.int32), -1)
-        out["tid"][:, s, :depth] = torch.where(live, 0, -1)
-        out["time_ns"][:, s, :depth] = torch.where(live, int(time_ns), -1)
-        out["count"][:, s] = cnt.to(torch.int32)
-        base = base + cnt
-    return out
-
-
 class Engine:
     """A lob_ctx with torch-allocated outputs.  All calls run on the current
     torch stream unless `stream` is given."""
@@ -354,6 +330,14 @@ class Engine:
         t = {k: bk[k].contiguous() for k in ("price", "qty", "oid", "tid", "time_ns", "count")}
         lob_set_book(self.h, t["price"], t["qty"], t["oid"], t["tid"], t["time_ns"], t["count"],
                      self.stream)
+
+    def init_from_levels(self, bid_px, bid_qty, ask_px, ask_qty, time_ns=0):
+        """Every book from a level snapshot (lob_init_from_levels, Sec. 5.1.1):
+        int32 CUDA tensors [n_books, depth] in the lob_get_levels layout."""
+        if bid_px.dim() != 2 or bid_px.shape[0] != self.n_books:
+            raise ValueError("level arrays must be [n_books, depth]")
+        t = [x.contiguous() for x in (bid_px, bid_qty, ask_px, ask_qty)]
+        lob_init_from_levels(self.h, *t, time_ns=time_ns, stream=self.stream)
 
     def stats(self):
         ctr = torch.empty((self.n_books, N_COUNTERS), dtype=torch.int64, device="cuda")

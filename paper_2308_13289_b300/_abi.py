@@ -40,6 +40,7 @@ SIGNATURES = {
     "lob_get_trades": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_get_book": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
     "lob_set_book": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
+    "lob_init_from_levels": (ctypes.c_int, [vp, vp, vp, vp, vp, i32, i64, vp]),
     "lob_get_stats": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_set_launch": (ctypes.c_int, [vp, i32, i32, i32]),
     "lob_launch_count": (i64, [vp]),

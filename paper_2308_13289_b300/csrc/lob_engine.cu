@@ -383,6 +383,59 @@ __global__ void k_set_book(char* state, int32_t* counts, int32_t n_books, int32_
     if (l == 0) counts[bx] = n;
 }
 
+// Books from a level snapshot (Sec. 5.1.1), warp per book: each side's listed
+// levels (those before the first with price or volume <= 0) become one order
+// each, in listed order, OIDs -9000 downward over the bid levels then the ask
+// levels, TID 0, time `time_ns`.  A side listed out of priority order is
+// loaded empty (LOB_STATUS_BAD_BOOK_LOAD).  depth <= capacity (host check).
+template <int K>
+__global__ void k_init_from_levels(char* state, int32_t* counts, int32_t n_books, int32_t depth,
+                                   const int32_t* __restrict__ bid_px,
+                                   const int32_t* __restrict__ bid_qty,
+                                   const int32_t* __restrict__ ask_px,
+                                   const int32_t* __restrict__ ask_qty, int64_t time_ns,
+                                   int32_t* status)
+{
+    const int l = lane_id();
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= n_books) return;
+    int32_t oid_next = kSnapshotOidMax;  // first snapshot OID, -9000
+    for (int x = 0; x < 2; ++x) {
+        const int32_t* px = (x == 0 ? bid_px : ask_px) + b * depth;
+        const int32_t* qt = (x == 0 ? bid_qty : ask_qty) + b * depth;
+        // listed levels: the prefix before the first level with P <= 0 or Q <= 0
+        int n = 0;
+        for (int k0 = 0; k0 < depth; k0 += 32) {
+            const int k = k0 + l;
+            const bool ok = k < depth && px[k] > 0 && qt[k] > 0;
+            const unsigned gap = ~__ballot_sync(kFull, ok);
+            const int m = gap ? __ffs(gap) - 1 : 32;
+            n += m;
+            if (m < 32) break;
+        }
+        // priority order: bids non-increasing, asks non-decreasing
+        bool bad = false;
+        for (int k = 1 + l; k < n; k += 32)
+            bad = bad || (x == 0 ? px[k] > px[k - 1] : px[k] < px[k - 1]);
+        bad = __any_sync(kFull, bad);
+        char* side = state + b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
+        const int n_load = bad ? 0 : n;
+        for (int r = l; r < n_load; r += 32) {  // priority rank r = listed level r
+            const int i = storage_index<K>(r, n_load);
+            reinterpret_cast<int32_t*>(side + Geo<K>::PX)[i] = px[r];
+            reinterpret_cast<int32_t*>(side + Geo<K>::QTY)[i] = qt[r];
+            reinterpret_cast<int32_t*>(side + Geo<K>::OID)[i] = oid_next - r;
+            reinterpret_cast<int32_t*>(side + Geo<K>::TID)[i] = 0;
+            reinterpret_cast<int64_t*>(side + Geo<K>::TM)[i] = time_ns;
+        }
+        oid_next -= n;  // the OIDs count every listed level, loaded or not
+        if (l == 0) {
+            counts[2 * b + x] = n_load;
+            if (bad) atomicOr(status, LOB_STATUS_BAD_BOOK_LOAD);
+        }
+    }
+}
+
 __global__ void k_reset_books(const int32_t* __restrict__ ids, int32_t n, int32_t n_books,
                               int32_t* counts, int64_t* tcounts, int64_t* stats, int32_t* status)
 {
@@ -1002,6 +1055,32 @@ int lob_set_book(lob_ctx* c, const int32_t* px, const int32_t* qty, const int32_
     return LOB_OK;
 }
 
+int lob_init_from_levels(lob_ctx* c, const int32_t* d_bid_px, const int32_t* d_bid_qty,
+                         const int32_t* d_ask_px, const int32_t* d_ask_qty, int32_t depth,
+                         int64_t time_ns, void* stream)
+{
+    if (!c || !d_bid_px || !d_bid_qty || !d_ask_px || !d_ask_qty) {
+        lob_set_error("lob_init_from_levels: null argument");
+        return LOB_E_INVAL;
+    }
+    if (depth < 1 || depth > c->cfg.capacity) {
+        lob_set_error("lob_init_from_levels: depth %d outside 1..capacity (%d)", depth,
+                      c->cfg.capacity);
+        return LOB_E_INVAL;
+    }
+    const int wpb = 8;
+    dim3 grid((unsigned)((c->cfg.n_books + wpb - 1) / wpb)), block(32 * wpb);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = c->cfg.n_books;
+    LOB_DISPATCH_K(c->K, (k_init_from_levels<KK><<<grid, block, 0, s>>>(
+                             c->d_state, c->d_counts, nb, depth, d_bid_px, d_bid_qty, d_ask_px,
+                             d_ask_qty, time_ns, c->d_status)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_init_from_levels");
+    c->launches += 1;
+    return LOB_OK;
+}
+
 int lob_get_stats(lob_ctx* c, int64_t* d_counters, int32_t* d_status, void* stream)
 {
     if (!c) {
@@ -1058,6 +1137,26 @@ struct StaticSetup {
 };
 StaticSetup g_static[kMaxDevices];
 std::mutex g_static_mu;
+
+// scratch layout: [queue: 256 B][counts: n_books*2 int32, padded to 256 B][book state]
+size_t static_state_offset(int64_t n_books)
+{
+    return 256 + (((size_t)n_books * 8 + 255) / 256) * 256;
+}
+
+size_t static_scratch_bytes(int64_t n_books, int K)
+{
+    return static_state_offset(n_books) + (size_t)n_books * (size_t)lob_book_bytes(K);
+}
+
+// the largest n_books whose scratch fits (exact)
+int static_max_books(int K)
+{
+    int64_t n = (int64_t)(kStaticScratchBytes - 256) / ((int64_t)lob_book_bytes(K) + 8);
+    while (n > 0 && static_scratch_bytes(n, K) > kStaticScratchBytes) --n;
+    while (static_scratch_bytes(n + 1, K) <= kStaticScratchBytes) ++n;
+    return (int)n;
+}
 
 constexpr int kStaticChunk = 64;
 int static_warps(int K) { return K >= 8 ? 4 : 8; }
@@ -1120,16 +1219,14 @@ extern "C" int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t
         return LOB_E_INVAL;
     }
     const int K = k_of(capacity);
-    // scratch layout: [queue: 256 B][counts: n_books*2 int32, 256-aligned][book state]
     const size_t counts_off = 256;
-    const size_t state_off = counts_off + (((size_t)n_books * 8 + 255) / 256) * 256;
-    const size_t need = state_off + (size_t)n_books * (size_t)lob_book_bytes(K);
+    const size_t state_off = static_state_offset(n_books);
+    const size_t need = static_scratch_bytes(n_books, K);
     if (need > kStaticScratchBytes) {
         lob_set_error("lob_process_streams_static: %d books of capacity %d need %zu bytes of "
-                      "scratch, more than the library's fixed %zu bytes (at most %zu books at "
+                      "scratch, more than the library's fixed %zu bytes (at most %d books at "
                       "this capacity)",
-                      n_books, capacity, need, kStaticScratchBytes,
-                      (kStaticScratchBytes - 512) / ((size_t)lob_book_bytes(K) + 8));
+                      n_books, capacity, need, kStaticScratchBytes, static_max_books(K));
         return LOB_E_INVAL;
     }
     int dev = 0;
@@ -1153,6 +1250,8 @@ extern "C" int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t
     if (e == cudaSuccess)
         e = cudaMemsetAsync(d_counters, 0, (size_t)n_books * kNumCtr * sizeof(int64_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
+    // every book's count is defined, also for one that is skipped (bad segment)
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_trade_counts, 0, (size_t)n_books * 8, st);
     if (e != cudaSuccess) return lob_cuda_fail(e, "lob_process_streams_static memset");
 
     ProcArgs a;

@@ -7,10 +7,11 @@ to the snapshot order resting at the cancel's price.  The paper writes the OID
 range as [-inf, -9000] but the cancel condition as OID < -9000; this build
 reads both as OID <= -9000 (the first snapshot order is cancellable too).
 
-CPU: a hand-worked example pins the oracle's rule, and the layout that the
-package's snapshot helper builds.  GPU: the CUDA path against the oracle on
-seeded snapshots plus streams whose cancels name unknown OIDs at snapshot
-prices, in the register-resident (capacity <= 128) and grouped shared-memory
+CPU: hand-worked examples pin the oracle's snapshot initialisation (OID
+order, short and out-of-order sides, equal prices) and its cancel rule.  GPU:
+lob_init_from_levels against the oracle's own initialisation from the same
+level arrays, then streams whose cancels name unknown OIDs at snapshot prices,
+in the register-resident (capacity <= 128) and grouped shared-memory
 (capacity > 128) book layouts.
 """
 import numpy as np
@@ -104,23 +105,67 @@ def test_oracle_snapshot_orders_trade_like_any_order():
     assert _levels(o) == ([(99, 6)], [(103, 6)])
 
 
-def test_snapshot_books_layout():
-    torch = pytest.importorskip("torch")
-    import paper_2308_13289_b300 as eng
-    bp = torch.tensor([[100, 99, 98], [50, -1, 48]], dtype=torch.int32)
-    bq = torch.tensor([[5, 7, 1], [3, 0, 9]], dtype=torch.int32)
-    ap = torch.tensor([[101, 103, -1], [51, 52, 53]], dtype=torch.int32)
-    aq = torch.tensor([[4, 6, 0], [2, 2, 2]], dtype=torch.int32)
-    bk = eng.snapshot_books(bp, bq, ap, aq, capacity=4, time_ns=77)
-    assert bk["count"].tolist() == [[3, 2], [1, 3]]
-    assert bk["oid"][0].tolist() == [[-9000, -9001, -9002, -1], [-9003, -9004, -1, -1]]
-    assert bk["oid"][1].tolist() == [[-9000, -1, -1, -1], [-9001, -9002, -9003, -1]]
-    assert bk["price"][1, 0].tolist() == [50, -1, -1, -1]
-    assert bk["qty"][0, 1].tolist() == [4, 6, -1, -1]
-    assert bk["time_ns"][0, 0].tolist() == [77, 77, 77, -1]
-    assert bk["tid"][1, 1].tolist() == [0, 0, 0, -1]
-    with pytest.raises(ValueError):
-        eng.snapshot_books(bp, bq, ap, aq, capacity=2)
+def _levels_case():
+    """Three books' level snapshots, depth 3 (int32 [3][3] per array).
+    book 0: bids 100x5, 99x7, 98x1; asks 101x4, 103x6, then an empty level
+    book 1: bids 50x3, then a level with volume 0 (the side ends there, the
+            48x9 after it is not listed); asks 51x2, 52x2, 53x2
+    book 2: bids 100x1, 101x1 (out of priority order: the side loads empty but
+            its two levels still use OIDs -9000, -9001); asks 102x1, 102x3
+            (equal prices: two orders at one level, in listed order)"""
+    bp = np.array([[100, 99, 98], [50, 49, 48], [100, 101, -1]], np.int32)
+    bq = np.array([[5, 7, 1], [3, 0, 9], [1, 1, 0]], np.int32)
+    ap = np.array([[101, 103, -1], [51, 52, 53], [102, 102, -1]], np.int32)
+    aq = np.array([[4, 6, 0], [2, 2, 2], [1, 3, 0]], np.int32)
+    return bp, bq, ap, aq
+
+
+# the books the snapshot reading gives, worked out by hand (capacity 4)
+HAND_INIT = {
+    "count": [[3, 2], [1, 3], [0, 2]],
+    "price": [[[100, 99, 98, -1], [101, 103, -1, -1]],
+              [[50, -1, -1, -1], [51, 52, 53, -1]],
+              [[-1, -1, -1, -1], [102, 102, -1, -1]]],
+    "qty": [[[5, 7, 1, -1], [4, 6, -1, -1]],
+            [[3, -1, -1, -1], [2, 2, 2, -1]],
+            [[-1, -1, -1, -1], [1, 3, -1, -1]]],
+    "oid": [[[-9000, -9001, -9002, -1], [-9003, -9004, -1, -1]],
+            [[-9000, -1, -1, -1], [-9001, -9002, -9003, -1]],
+            [[-1, -1, -1, -1], [-9002, -9003, -1, -1]]],
+    "tid": [[[0, 0, 0, -1], [0, 0, -1, -1]],
+            [[0, -1, -1, -1], [0, 0, 0, -1]],
+            [[-1, -1, -1, -1], [0, 0, -1, -1]]],
+    "time_ns": [[[77, 77, 77, -1], [77, 77, -1, -1]],
+                [[77, -1, -1, -1], [77, 77, 77, -1]],
+                [[-1, -1, -1, -1], [77, 77, -1, -1]]],
+}
+
+
+def test_oracle_init_from_levels_hand_worked():
+    o = oracle.Oracle(3, 4, 8)
+    assert o.init_from_levels(*_levels_case(), time_ns=77) == 1  # book 2's bid side
+    bk = o.book()
+    for k, v in HAND_INIT.items():
+        assert bk[k].tolist() == v, k
+    # the levels of the loaded books read back as the snapshot listed them
+    bpx, bqty, apx, aqty = o.levels(3)
+    assert bpx[0].tolist() == [100, 99, 98] and bqty[0].tolist() == [5, 7, 1]
+    assert apx[2].tolist() == [102, -1, -1] and aqty[2].tolist() == [4, 0, 0]
+    assert o.trades()[1].tolist() == [0, 0, 0]
+
+
+def test_oracle_init_from_levels_then_cancel_by_price():
+    # the initialised book equals the hand-built one the cancel-rule example uses
+    cap = 8
+    bp = np.array([[100, 99]], np.int32)
+    bq = np.array([[5, 7]], np.int32)
+    ap = np.array([[101, 103]], np.int32)
+    aq = np.array([[4, 6]], np.int32)
+    o = oracle.Oracle(1, cap, 16, snapshot_cancels=True)
+    o.init_from_levels(bp, bq, ap, aq, time_ns=0)
+    ref = _hand_snapshot(cap)
+    for k, v in o.book().items():
+        assert np.array_equal(v, ref[k]), k
 
 
 def _snapshot_workload(n_books, depth, n_msgs, seed):
@@ -177,20 +222,20 @@ def test_gpu_snapshot_cancels_match_oracle(cap):
     (bp, bq, ap, aq), msgs, off = _snapshot_workload(n_books, depth, n_msgs, 4242 + cap)
     tcap = 4096
     t = [torch.from_numpy(x).cuda() for x in (bp, bq, ap, aq)]
-    bk = eng.snapshot_books(*t, capacity=cap, time_ns=0)
     e = eng.Engine(n_books, cap, tcap, snapshot_cancels=True)
-    e.set_book(bk)
+    e.init_from_levels(*t, time_ns=0)
     e.process_batch(eng.messages_to_device(msgs), torch.from_numpy(off).cuda())
     g = gpu_outputs(e)
     e.close()
+    # the oracle builds its own books from the same level arrays
     o = oracle.Oracle(n_books, cap, tcap, snapshot_cancels=True)
-    o.set_book({k: v.cpu().numpy() for k, v in bk.items()})
+    assert o.init_from_levels(bp, bq, ap, aq, time_ns=0) == 0
     o.process(msgs, off)
     ref = oracle_outputs(o)
     assert_same(g, ref)
     # the workload really exercises the rule: more cancels hit than without it
     off_rule = oracle.Oracle(n_books, cap, tcap)
-    off_rule.set_book({k: v.cpu().numpy() for k, v in bk.items()})
+    off_rule.init_from_levels(bp, bq, ap, aq, time_ns=0)
     off_rule.process(msgs, off)
     hit = oracle.COUNTERS.index("cancel_hit")
     assert ref["counters"][:, hit].sum() > off_rule.counters()[:, hit].sum() + 100
@@ -204,13 +249,69 @@ def test_gpu_snapshot_flag_off_ignores_unknown_ids():
     n_books, depth, n_msgs, cap, tcap = 32, 10, 800, 64, 2048
     (bp, bq, ap, aq), msgs, off = _snapshot_workload(n_books, depth, n_msgs, 99)
     t = [torch.from_numpy(x).cuda() for x in (bp, bq, ap, aq)]
-    bk = eng.snapshot_books(*t, capacity=cap)
     e = eng.Engine(n_books, cap, tcap)
-    e.set_book(bk)
+    e.init_from_levels(*t)
     e.process_batch(eng.messages_to_device(msgs), torch.from_numpy(off).cuda())
     g = gpu_outputs(e)
     e.close()
     o = oracle.Oracle(n_books, cap, tcap)
-    o.set_book({k: v.cpu().numpy() for k, v in bk.items()})
+    o.init_from_levels(bp, bq, ap, aq)
     o.process(msgs, off)
     assert_same(g, oracle_outputs(o))
+
+
+def _random_levels(n_books, depth, seed):
+    """Level snapshots with every case the reading names: full and short
+    sides, empty sides, levels of equal price, sides out of priority order."""
+    rng = np.random.default_rng(seed)
+    mid = rng.integers(1_000, 50_000, n_books)
+    gaps = rng.integers(0, 3, (n_books, depth))  # 0: a level at the previous price
+    bp = (mid[:, None] - np.cumsum(gaps, axis=1)).astype(np.int32)
+    ap = (mid[:, None] + 1 + np.cumsum(gaps[:, ::-1], axis=1)).astype(np.int32)
+    bq = rng.integers(1, 1_000, (n_books, depth)).astype(np.int32)
+    aq = rng.integers(1, 1_000, (n_books, depth)).astype(np.int32)
+    for arr_p, arr_q in ((bp, bq), (ap, aq)):
+        cut = rng.integers(0, depth + 1, n_books)      # listed levels per side
+        for b in range(n_books):
+            if rng.random() < 0.5:
+                arr_p[b, cut[b]:] = np.where(rng.random(depth - cut[b]) < 0.5, -1, 0)
+                arr_q[b, cut[b]:] = np.where(arr_p[b, cut[b]:] < 0, 0, rng.integers(0, 9))
+    swap = rng.random(n_books) < 0.1                   # out of priority order
+    bp[swap, 0], bp[swap, -1] = bp[swap, -1].copy(), bp[swap, 0].copy()
+    return bp, bq, ap, aq
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cap,depth", [(7, 7), (32, 10), (100, 10), (128, 64), (300, 40),
+                                       (512, 512)])
+def test_gpu_init_from_levels_matches_oracle(cap, depth):
+    """lob_init_from_levels against the oracle's own snapshot initialisation:
+    canonical books, levels and the status bit of sides loaded empty."""
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    n_books = 96
+    bp, bq, ap, aq = _random_levels(n_books, depth, 100 + cap)
+    e = eng.Engine(n_books, cap, 16)
+    e.init_from_levels(*[torch.from_numpy(x).cuda() for x in (bp, bq, ap, aq)], time_ns=123456789)
+    g = gpu_outputs(e)
+    _, st = e.stats()
+    e.close()
+    o = oracle.Oracle(n_books, cap, 16)
+    emptied = o.init_from_levels(bp, bq, ap, aq, time_ns=123456789)
+    ref = oracle_outputs(o)
+    assert_same(g, ref)
+    assert emptied > 0
+    assert int(st.item()) == eng.STATUS_BAD_BOOK_LOAD
+
+
+@pytest.mark.gpu
+def test_gpu_init_from_levels_rejects_bad_depth():
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    e = eng.Engine(4, 8, 16)
+    z = torch.ones((4, 9), dtype=torch.int32, device="cuda")
+    with pytest.raises(eng.LobError):
+        e.init_from_levels(z, z, z, z)  # depth 9 > capacity 8
+    e.close()
