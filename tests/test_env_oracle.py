@@ -30,6 +30,9 @@ def load_env_fixture(path):
             cur["trades"].append(tuple(int(x) for x in r))
         elif k == "sums":
             cur["sums"] = tuple(int(x) for x in r)
+        elif k == "reward":
+            # lambda -> float32 bit pattern written by hand
+            cur.setdefault("reward", {})[float(r[0])] = int(r[2], 16)
         elif k in ("lbid", "lask"):
             v = [int(x) for x in r]
             cur[k] = [(v[0], v[1]), (v[2], v[3])]
@@ -40,20 +43,17 @@ def load_env_fixture(path):
     return cfg, steps, final, counters
 
 
-def reward_from_sums(sq, spq, aq, apq, lam, p_init):
-    """eq. rewardfunc with eq. vwap, evaluated by hand in IEEE double."""
-    if sq == 0 or aq == 0:
-        return np.float32(0.0)
-    vwap = float(spq) / float(sq)
-    adv = float(apq) - float(aq) * vwap
-    drift = lam * (float(aq) * (vwap - p_init))
-    return np.float32(adv + drift)
+ENV_FIXTURES = ["env_three_steps.env", "env_two_steps_mixed.env"]
 
 
+def reward_bits(x):
+    return int(np.asarray(x, dtype=np.float32).view(np.uint32))
+
+
+@pytest.mark.parametrize("fixture", ENV_FIXTURES)
 @pytest.mark.parametrize("lam", [0.0, 0.5])
-def test_env_oracle_hand_worked_episode(lam):
-    cfg, steps, final, counters = load_env_fixture(
-        os.path.join(HERE, "golden", "env_three_steps.env"))
+def test_env_oracle_hand_worked_episode(fixture, lam):
+    cfg, steps, final, counters = load_env_fixture(os.path.join(HERE, "golden", fixture))
     env = oracle.EnvOracle(1, cfg["capacity"], 64, n_steps=cfg["n_steps"],
                            parent_qty=cfg["parent"], agent_tid=cfg["agent_tid"],
                            depth=cfg["depth"], p_init_fallback=cfg["p_init_fallback"], lam=lam)
@@ -65,8 +65,8 @@ def test_env_oracle_hand_worked_episode(lam):
         assert got == st["trades"], st["step"]
         sq, spq, aq, apq = st["sums"]
         assert tuple(fills[0]) == (aq, apq)
-        exp = reward_from_sums(sq, spq, aq, apq, lam, final["p_init"])
-        assert reward[0].tobytes() == exp.tobytes(), (st["step"], reward[0], exp)
+        # the reward's float32 bits against the value worked out by hand
+        assert reward_bits(reward[0]) == st["reward"][lam], (st["step"], float(reward[0]))
         bp, bq, ap, aq_ = lv
         assert [(int(bp[0, k]), int(bq[0, k])) for k in range(2)] == st["lbid"]
         assert [(int(ap[0, k]), int(aq_[0, k])) for k in range(2)] == st["lask"]

@@ -12,7 +12,7 @@ import torch
 import lobgen
 import oracle
 from engine_harness import assert_same, gpu_outputs, oracle_outputs
-from test_env_oracle import load_env_fixture
+from test_env_oracle import ENV_FIXTURES, load_env_fixture, reward_bits
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -87,8 +87,9 @@ def compare(e, env, gout, oenv, oouts, n_steps):
     assert_same(gpu_outputs(e), oracle_outputs(oenv.books))
 
 
-def test_hand_worked_episode_on_gpu(eng):
-    cfg, steps, final, _ = load_env_fixture(os.path.join(HERE, "golden", "env_three_steps.env"))
+@pytest.mark.parametrize("fixture", ENV_FIXTURES)
+def test_hand_worked_episode_on_gpu(eng, fixture):
+    cfg, steps, final, _ = load_env_fixture(os.path.join(HERE, "golden", fixture))
     per = max(len(s["msgs"]) for s in steps)
     rows = []
     for s in steps:  # pad each window at its front with type-0 messages
@@ -112,9 +113,10 @@ def test_hand_worked_episode_on_gpu(eng):
         torch.cuda.synchronize()
         g = {k: v.cpu().numpy() for k, v in out.items()}
         compare(e, env, g, oenv, oouts, cfg["n_steps"])
-        # and the hand-worked sums themselves
+        # and the hand-worked sums and rewards themselves
         for t, s in enumerate(steps):
             assert tuple(g["fills"][t][0]) == s["sums"][2:]
+            assert reward_bits(g["reward"][t][0]) == s["reward"][lam], (t, lam)
 
 
 @pytest.mark.parametrize("splits,lam", [([1] * 40, 0.0), ([40], 0.25), ([17, 23], 0.0)])

@@ -1,8 +1,9 @@
 """The oracle's pins must catch plausible mistakes.  Each case copies the
 oracle source to a temporary directory, plants ONE mistake (a dropped term, a
 wrong sign, a wrong index or comparison), compiles it there, and checks that
-the hand-worked examples or the brute-force cross-check reject it.  Nothing is
-planted in the real oracle."""
+the hand-worked examples reject it: the book examples for the matching rules,
+the hand-worked environment episodes (rewards as literal float32 bits) for the
+reward of eqs. rewardfunc / vwap.  Nothing is planted in the real oracle."""
 import ctypes
 import itertools
 import os
@@ -13,6 +14,9 @@ import pytest
 
 import oracle
 from golden_format import cases, side_rows, trade_rows
+from test_env_oracle import ENV_FIXTURES, load_env_fixture, reward_bits
+
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lob_oracle.cpp")
 
@@ -30,6 +34,21 @@ MUTANTS = {
                        "!own.strictly_better(own.worst().price, m.price)"),
     "market_rests": ("bk.counters[C_MARKET_DISCARDED_QTY] += rest;",
                      "bk.counters[C_MARKET_DISCARDED_QTY] += rest; if (rest > 0) add(E, bk, m, rest);"),
+}
+
+
+# mistakes in the environment's reward (Sec. 5.2.4): each changes at least one
+# hand-worked reward of the two golden episodes
+REWARD_MUTANTS = {
+    "advantage_sign": ("(double)sums.apq - (double)sums.aq * vwap;",
+                       "(double)sums.aq * vwap - (double)sums.apq;"),
+    "advantage_uses_all_trades_qty": ("(double)sums.apq - (double)sums.aq * vwap;",
+                                      "(double)sums.apq - (double)sums.sq * vwap;"),
+    "vwap_over_agent_trades": ("(double)sums.spq / (double)sums.sq;",
+                               "(double)sums.apq / (double)sums.aq;"),
+    "drift_sign": ("(vwap - es.p_init)", "(es.p_init - vwap)"),
+    "drift_drops_quantity": ("cfg.lambda * ((double)sums.aq * (vwap - es.p_init))",
+                             "cfg.lambda * (vwap - es.p_init)"),
 }
 
 
@@ -86,3 +105,50 @@ def test_unmutated_copy_passes(tmp_path):
     lib = ctypes.CDLL(_build_mutant(tmp_path, "identity", "int oracle_abi_version(void) { return 1; }",
                                     "int oracle_abi_version(void) { return 1; }"))
     assert _golden_ok(lib)
+
+
+def _env_golden_ok(lib):
+    """Run both hand-worked episodes (lambda 0 and 1/2) through a compiled
+    oracle and compare every reward's bits with the literal ones."""
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.oracle_env_create.restype = vp
+    lib.oracle_env_create.argtypes = [i32] * 10 + [ctypes.c_double]
+    lib.oracle_env_step.argtypes = [vp, vp, vp, vp, vp, i32] + [vp] * 6 + [i32, vp]
+    lib.oracle_env_destroy.argtypes = [vp]
+    for fx in ENV_FIXTURES:
+        cfg, steps, _, _ = load_env_fixture(os.path.join(HERE, "golden", fx))
+        for lam in (0.0, 0.5):
+            h = lib.oracle_env_create(1, cfg["capacity"], 64, cfg["n_steps"], cfg["parent"],
+                                      cfg["agent_tid"], cfg["depth"], cfg["p_init_fallback"], 2, 1,
+                                      lam)
+            ok = True
+            for st in steps:
+                m = oracle.messages(st["msgs"])
+                off = np.array([0, len(m)], np.int64)
+                draw = np.array([st["draw"]], np.uint32)
+                reward = np.empty(1, np.float32)
+                lv = [np.empty((1, cfg["depth"]), np.int32) for _ in range(4)]
+                fills = np.empty((1, 2), np.int64)
+                lib.oracle_env_step(h, vp(m.ctypes.data), vp(off.ctypes.data),
+                                    vp(draw.ctypes.data), None, st["step"],
+                                    vp(reward.ctypes.data), *[vp(x.ctypes.data) for x in lv],
+                                    vp(fills.ctypes.data), 1, None)
+                ok = ok and reward_bits(reward[0]) == st["reward"][lam]
+            lib.oracle_env_destroy(h)
+            if not ok:
+                return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(REWARD_MUTANTS))
+def test_env_golden_episodes_reject_reward_mutant(tmp_path, name):
+    old, new = REWARD_MUTANTS[name]
+    lib = ctypes.CDLL(_build_mutant(tmp_path, name, old, new))
+    assert not _env_golden_ok(lib), "planted reward mistake %r went unnoticed" % name
+
+
+def test_unmutated_copy_passes_env_episodes(tmp_path):
+    lib = ctypes.CDLL(_build_mutant(tmp_path, "identity_env",
+                                    "int oracle_abi_version(void) { return 1; }",
+                                    "int oracle_abi_version(void) { return 1; }"))
+    assert _env_golden_ok(lib)
