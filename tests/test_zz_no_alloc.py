@@ -99,3 +99,26 @@ def test_static_entry_point_refuses_oversized_requests():
                                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == -1
     assert b"scratch" in lib.lob_last_error()
+
+
+@pytest.mark.parametrize("cap,n_max", [(100, 5454), (512, 1364)])
+def test_static_entry_point_size_limit_is_exact(cap, n_max):
+    """256 + roundup(8 n, 256) + n * 48 * S <= 32 MiB (S = capacity rounded up
+    to 128 or 512 slots here): the largest n is accepted, n + 1 is refused.
+    Every segment is empty, so the accepted call only clears its outputs."""
+    lib = _lib()
+    m = torch.zeros((8, 8), dtype=torch.int32, device="cuda")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for n, rc_want in ((n_max, 0), (n_max + 1, -1)):
+        off = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+        cnt = torch.full((n,), 9, dtype=torch.int64, device="cuda")
+        ctr = torch.full((n, 20), 9, dtype=torch.int64, device="cuda")
+        st = torch.full((1,), 9, dtype=torch.int32, device="cuda")
+        rc = lib.lob_process_streams_static(_p(m), _p(off), n, cap, 0, 0, None, _p(cnt), _p(ctr),
+                                            None, None, None, None, None, None, _p(st), stream)
+        assert rc == rc_want, (n, lib.lob_last_error())
+        if rc == 0:
+            torch.cuda.synchronize()
+            assert int(cnt.abs().sum()) == 0 and int(ctr.abs().sum()) == 0 and int(st.item()) == 0
+        else:
+            assert ("at most %d books" % n_max).encode() in lib.lob_last_error()
