@@ -1,25 +1,36 @@
 """Continuous-batching server for order-book simulation episodes.
 
-An episode is a book of a given capacity that advances one step (a window of
-data messages, then its top levels) per tick for its length in steps -- the
-serving counterpart of the batched environments of Sec. 5.  Its message
-windows are loaded into HBM when the request is accepted (the paper likewise
-pre-loads fixed-size message windows, Sec. 5.1.1).  The server keeps the book
-of every admitted episode resident (one slot of a per-capacity pool), admits a
-waiting episode as soon as a slot of its capacity is free and its resident
-footprint fits the HBM budget, and on every tick advances ALL admitted
-episodes by one step: per capacity class one launch over the active slots'
-current windows (lob_process_segments), each class on its own CUDA stream so
-the classes overlap on the device.  Episodes that finish free their slot in
-the same tick, so later arrivals join a batch that is already running.
+An episode is a book of a given capacity that advances one step per tick for
+its length in steps: a window of data messages is produced for it on the
+device (the seeded generator stands in for the market-data feed; the paper
+replays fixed-size message windows step by step, Sec. 5.1.1), the window is
+applied to the book, and the book's top levels are written -- the serving
+counterpart of the batched environments of Sec. 5.
 
-The host runs up to RING ticks ahead of the GPU (finishing times are known
-from the step counts, so no tick waits for the previous one); the latency of
-an episode-step is the GPU time of its pool's tick, measured by events around
-that tick's work on the pool's stream.  The report gives p50/p99 over all
-episode-steps, steps/s and messages/s, the admission wait and the queue length
-over time.  (With collect=True, used by the tests, every tick is synchronous
-and timed on the host.)
+Admission by HBM footprint.  The book of every admitted episode stays resident
+in one slot of a per-capacity pool.  A waiting episode is admitted, in arrival
+order, as soon as a slot of its capacity is free and its footprint -- book
+state, trade log, counters, generator state and its step window -- fits the
+HBM budget beside the episodes already running.  Episodes that finish free
+their slot and their footprint in the same tick, so later arrivals join a
+batch that is already running.
+
+Every tick advances ALL admitted episodes by one step.  Per capacity class:
+one generator launch writes the active slots' windows on the pool's generator
+stream, one lob_process_batch launch applies them and one lob_get_levels
+launch reports the levels on the pool's processing stream.  The windows are
+double-buffered, so the generator produces tick k+1 while tick k is being
+processed; the classes run on their own streams and overlap on the device.
+
+The host runs up to RING ticks ahead of the GPU (finishing times follow from
+the step counts, so no tick waits for the previous one).  The latency of an
+episode-step is the GPU time of its pool's processing of the tick, from the
+moment its window is ready to the moment its levels are written, measured by
+events on the processing stream; the generator's time per tick is reported
+beside it.  With collect=True (tests) every tick is synchronous, timed on the
+host, and the per-step levels and trade counts of every episode are kept.
+keep_final=True keeps every episode's final book and counters, captured on the
+device in stream order when it finishes (valid in both modes).
 """
 from __future__ import annotations
 
@@ -32,10 +43,13 @@ import time
 import numpy as np
 import torch
 
-from . import Engine, lib, lob_get_levels
+import lobgen
+
+from . import N_COUNTERS, Engine, lib, lob_get_levels
 
 MSG_BYTES = 32
 RING = 8  # ticks the host may run ahead of the GPU
+GEN_STATE_BYTES = lobgen.STATE_BYTES + lobgen.DEFAULT_POOL * lobgen.POOL_ENTRY_BYTES
 
 
 @dataclasses.dataclass
@@ -45,7 +59,6 @@ class Episode:
     n_steps: int
     msgs_per_step: int
     arrival: float             # seconds (wall clock) or tick index (virtual clock)
-    base: int = -1             # first message of the episode in the payload buffer
     admitted: float = math.nan
     done: float = math.nan
 
@@ -66,157 +79,227 @@ def sample_episodes(rate: float, window: float, seed: int, capacities=(100, 250,
     return out
 
 
-def footprint_bytes(capacity: int, trade_capacity: int) -> int:
-    """Resident HBM an admitted episode holds: book state, trade log, counters."""
+def book_bytes(capacity: int) -> int:
+    """Device bytes of one book of this capacity (48 per slot, capacity
+    rounded up to a power-of-two multiple of 32 slots)."""
     k = 1
     while 32 * k < capacity:
         k *= 2
-    return 48 * 32 * k + 32 * trade_capacity + 8 * 24 + 64
+    return 48 * 32 * k
+
+
+def footprint_bytes(capacity: int, trade_capacity: int, msgs_per_step: int) -> int:
+    """HBM an admitted episode holds while it runs: its book (state and the two
+    side counts), its trade log and count, its counters, its generator state
+    and its step window."""
+    return (book_bytes(capacity) + 8 + 32 * trade_capacity + 8 + 8 * N_COUNTERS
+            + GEN_STATE_BYTES + MSG_BYTES * msgs_per_step)
+
+
+def _p(t, byte_off=0):
+    return ctypes.c_void_p(t.data_ptr() + byte_off)
 
 
 class _Pool:
-    """Resident slots of one capacity class (numpy bookkeeping, one stream)."""
+    """Resident slots of one capacity class: an engine context over all slots,
+    per-slot generator state, double-buffered step windows, two streams."""
 
-    def __init__(self, capacity, slots, trade_capacity, depth, collect):
-        self.capacity, self.slots, self.depth = capacity, slots, depth
-        self.stream = torch.cuda.Stream()
+    def __init__(self, capacity, slots, trade_capacity, depth, params, max_mps, collect):
+        self.capacity, self.slots, self.depth, self.params = capacity, slots, depth, params
+        self.max_mps = max_mps
+        self.stream = torch.cuda.Stream()   # processing
+        self.gstream = torch.cuda.Stream()  # window generation
+        S = slots
+        # packed per-tick upload (int64 words): offsets [S+1] | counts [S] |
+        # restart stream ids [S] | active slot ids (int32) [S] | restart slots (int32) [S]
+        self.o_cnt, self.o_sid, self.o_ids = S + 1, 2 * S + 1, 3 * S + 1
+        self.o_rid = self.o_ids + (S + 1) // 2
+        self.pack_words = self.o_rid + (S + 1) // 2
         with torch.cuda.stream(self.stream):
             self.engine = Engine(slots, capacity, trade_capacity, stream=self.stream)
-            # one packed upload per tick: [start | count | ids (int32 pairs)]
-            self.d_pack = torch.empty(3 * slots, dtype=torch.int64, device="cuda")
-            self.d_start = self.d_pack[:slots]
-            self.d_cnt = self.d_pack[slots:2 * slots]
-            self.d_ids = self.d_pack[2 * slots:].view(torch.int32)
-            self.levels = [torch.empty((slots, depth), dtype=torch.int32, device="cuda")
+            self.g_states = torch.zeros(S * lobgen.STATE_BYTES, dtype=torch.uint8, device="cuda")
+            self.g_pools = torch.zeros(S * params.pool_cap * lobgen.POOL_ENTRY_BYTES,
+                                       dtype=torch.uint8, device="cuda")
+            self.geo_px = torch.from_numpy(lobgen.GEO_PX.view(np.int64)).cuda()
+            self.geo_q = torch.from_numpy(lobgen.GEO_Q.view(np.int64)).cuda()
+            self.win = [torch.empty((S * max_mps, 8), dtype=torch.int32, device="cuda")
+                        for _ in range(2)]
+            self.d_pack = [torch.empty(self.pack_words, dtype=torch.int64, device="cuda")
+                           for _ in range(2)]
+            self.levels = [torch.empty((S, depth), dtype=torch.int32, device="cuda")
                            for _ in range(4)]
-            self.d_tcount = torch.empty(slots, dtype=torch.int64, device="cuda")
-            self.d_slot = torch.arange(slots, dtype=torch.int32, device="cuda")
-        # a ring of pinned staging sets, so the host can run ahead of the GPU;
-        # a set is reused only after the event recorded behind its copies
+            self.d_tcount = torch.empty(S, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        self.reserved_bytes = (S * (book_bytes(capacity) + 8 + 32 * trade_capacity + 8
+                                    + 8 * N_COUNTERS + GEN_STATE_BYTES)
+                               + 2 * S * max_mps * MSG_BYTES)
+        self.ev_gen = [torch.cuda.Event() for _ in range(2)]   # windows k ready
+        self.ev_used = [torch.cuda.Event() for _ in range(2)]  # windows k consumed
         self.ring = []
         for _ in range(RING):
-            pack = torch.empty(3 * slots, dtype=torch.int64).pin_memory()
-            self.ring.append(dict(pack=pack, np=pack.numpy(), used=torch.cuda.Event(),
+            pack = torch.empty(self.pack_words, dtype=torch.int64).pin_memory()
+            self.ring.append(dict(pack=pack, np=pack.numpy(), copied=torch.cuda.Event(),
+                                  g0=torch.cuda.Event(enable_timing=True),
+                                  g1=torch.cuda.Event(enable_timing=True),
                                   t0=torch.cuda.Event(enable_timing=True),
-                                  t1=torch.cuda.Event(enable_timing=True), busy=False))
+                                  t1=torch.cuda.Event(enable_timing=True),
+                                  busy=False, timed=False, n=0))
         self.ring_pos = 0
-        self.lat = []  # (GPU ms of a timed tick, episodes in it)
+        self.tick = 0
+        self.lat = []      # (GPU ms of a timed tick's processing, episodes in it)
+        self.gen_ms = []   # GPU ms of a timed tick's window generation
         self.free = list(range(slots - 1, -1, -1))
         self.ep = np.full(slots, -1, np.int64)      # episode index in the slot, -1 free
         self.step = np.zeros(slots, np.int64)
         self.n_steps = np.zeros(slots, np.int64)
         self.mps = np.zeros(slots, np.int64)
-        self.base = np.zeros(slots, np.int64)
+        self.restart = []  # (slot, stream id) admitted since the last tick
         self.n_active = 0
         self.collect = collect
 
-    def _retire_slot(self, st):
-        """Wait for a staging set's tick to finish and record its GPU time."""
-        st["used"].synchronize()
-        if st.get("timed"):
+    def _retire(self, st):
+        """Wait until a staging set's upload has landed; record its timings."""
+        st["copied"].synchronize()
+        if st["timed"]:
             st["t1"].synchronize()
             self.lat.append((st["t0"].elapsed_time(st["t1"]), st["n"]))
-        st["busy"] = False
-        st["timed"] = False
+            self.gen_ms.append(st["g0"].elapsed_time(st["g1"]))
+        st["busy"] = st["timed"] = False
 
     def flush(self):
         for st in self.ring:
             if st["busy"]:
-                self._retire_slot(st)
+                self._retire(st)
 
     def admit(self, idx: int, ep: Episode):
+        if ep.msgs_per_step > self.max_mps:
+            raise ValueError("episode %d: %d messages per step above the pool's %d"
+                             % (ep.id, ep.msgs_per_step, self.max_mps))
         s = self.free.pop()
         self.ep[s], self.step[s] = idx, 0
-        self.n_steps[s], self.mps[s], self.base[s] = ep.n_steps, ep.msgs_per_step, ep.base
+        self.n_steps[s], self.mps[s] = ep.n_steps, ep.msgs_per_step
+        self.restart.append((s, ep.id))
         self.n_active += 1
-        with torch.cuda.stream(self.stream):
-            self.engine.reset_books(self.d_slot[s:s + 1])
 
-    def launch_step(self, d_msgs, timing=False):
-        """One step of every active slot, asynchronously on this pool's stream.
-        Returns (active slots, messages, (start, end) events or None)."""
+    def launch_step(self, timing=False):
+        """One step of every active slot, asynchronously: windows on the
+        generator stream, processing and levels on the processing stream.
+        Returns (active slots, messages)."""
         act = np.flatnonzero(self.ep >= 0).astype(np.int32)
         n = len(act)
         cnt = self.mps[act]
         st = self.ring[self.ring_pos]
         self.ring_pos = (self.ring_pos + 1) % len(self.ring)
         if st["busy"]:
-            self._retire_slot(st)
-        sl = self.slots
+            self._retire(st)
         buf = st["np"]
-        buf[:n] = self.base[act] + self.step[act] * cnt
-        buf[sl:sl + n] = cnt
-        buf[2 * sl:].view(np.int32)[:n] = act
-        s = ctypes.c_void_p(self.stream.cuda_stream)
-        p = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
-        ev = None
-        with torch.cuda.stream(self.stream):
-            st["timed"] = timing
-            st["n"] = n
+        buf[0] = 0
+        np.cumsum(cnt, out=buf[1:n + 1])
+        buf[self.o_cnt:self.o_cnt + n] = cnt
+        nr = len(self.restart)
+        if nr:
+            rs = np.array(self.restart, dtype=np.int64)
+            buf[self.o_sid:self.o_sid + nr] = rs[:, 1]
+            buf[self.o_rid:].view(np.int32)[:nr] = rs[:, 0]
+        buf[self.o_ids:].view(np.int32)[:n] = act
+        self.restart = []
+        k = self.tick & 1
+        dp = self.d_pack[k]
+        lg = lobgen.cuda_lib()
+        gs, ps = self.gstream, self.stream
+        g_s = ctypes.c_void_p(gs.cuda_stream)
+        p_s = ctypes.c_void_p(ps.cuda_stream)
+        # generator stream: the windows of this tick (buffer k is free once
+        # the processing of tick-2 has consumed it)
+        gs.wait_event(self.ev_used[k])
+        with torch.cuda.stream(gs):
+            dp.copy_(st["pack"], non_blocking=True)
+            st["copied"].record(gs)
+            st["busy"], st["timed"], st["n"] = True, timing, n
             if timing:
-                ev = (st["t0"], st["t1"])
-                ev[0].record(self.stream)
-            self.d_pack.copy_(st["pack"], non_blocking=True)
-            st["used"].record(self.stream)
-            st["busy"] = True
-            rc = lib().lob_process_segments(self.engine.h, p(d_msgs), p(self.d_start),
-                                            p(self.d_cnt), p(self.d_ids), n, s)
-            if rc != 0:
-                raise RuntimeError("lob_process_segments failed")
-            lob_get_levels(self.engine.h, self.depth, *self.levels, stream=self.stream)
+                st["g0"].record(gs)
+            if nr and lg.lobgen_dev_init_ids(ctypes.byref(self.params), nr, _p(dp, 8 * self.o_rid),
+                                             _p(dp, 8 * self.o_sid), _p(self.g_states), g_s) != 0:
+                raise RuntimeError("lobgen_dev_init_ids failed")
+            if lg.lobgen_dev_advance(ctypes.byref(self.params), _p(self.geo_px), _p(self.geo_q), n,
+                                     _p(dp, 8 * self.o_ids), _p(self.g_states), _p(self.g_pools),
+                                     _p(dp, 8 * self.o_cnt), _p(dp), _p(self.win[k]), g_s) != 0:
+                raise RuntimeError("lobgen_dev_advance failed")
+            if timing:
+                st["g1"].record(gs)
+            self.ev_gen[k].record(gs)
+        # processing stream
+        ps.wait_event(self.ev_gen[k])
+        with torch.cuda.stream(ps):
+            if timing:
+                st["t0"].record(ps)
+            h = self.engine.h
+            if nr and lib().lob_reset_books(h, _p(dp, 8 * self.o_rid), nr, p_s) != 0:
+                raise RuntimeError("lob_reset_books failed")
+            if lib().lob_process_batch(h, _p(self.win[k]), _p(dp), _p(dp, 8 * self.o_ids), n,
+                                       p_s) != 0:
+                raise RuntimeError("lob_process_batch failed")
+            lob_get_levels(h, self.depth, *self.levels, stream=ps)
             if self.collect:
-                lib().lob_get_trades(self.engine.h, None, p(self.d_tcount), s)
+                lib().lob_get_trades(h, None, _p(self.d_tcount), p_s)
             if timing:
-                ev[1].record(self.stream)
-        return act, int(cnt.sum()), ev
+                st["t1"].record(ps)
+            self.ev_used[k].record(ps)
+        self.tick += 1
+        return act, int(cnt.sum())
+
+    def capture_final(self):
+        """The pool's books and counters as they stand once the work queued so
+        far has run (device tensors, filled in stream order)."""
+        with torch.cuda.stream(self.stream):
+            bk = self.engine.book()
+            ctr, _ = self.engine.stats()
+        return bk, ctr
 
 
 class Server:
     """Continuous batching over per-capacity slot pools with HBM admission."""
 
     def __init__(self, capacities=(100, 250, 500), hbm_budget=2 << 30, trade_capacity=2048,
-                 depth=10, seed=20230829, max_slots=4096, collect=False):
-        import lobgen
-        self.lobgen = lobgen
+                 depth=10, seed=20230829, max_slots=4096, collect=False, keep_final=False,
+                 msgs_per_step=(100, 500)):
         self.params = lobgen.make_params(seed, "pm1")
         self.depth = depth
         self.budget = hbm_budget
-        self.fp = {c: footprint_bytes(c, trade_capacity) for c in capacities}
-        self.pools = {c: _Pool(c, min(max_slots, max(1, hbm_budget // self.fp[c])),
-                               trade_capacity, depth, collect)
-                      for c in capacities}
-        self.used = 0
+        self.tcap = trade_capacity
         self.collect = collect
+        self.keep_final = keep_final or collect
+        lo, hi = msgs_per_step
+        self.pools = {}
+        for c in capacities:
+            # as many slots as the budget holds of the smallest episodes
+            slots = int(min(max_slots, max(1, hbm_budget // footprint_bytes(c, trade_capacity, lo))))
+            self.pools[c] = _Pool(c, slots, trade_capacity, depth, self.params, hi, collect)
+        self.used = 0
         self.records = collections.defaultdict(list)  # episode id -> per-step outputs
         self.final_books = {}
+        self.final_counters = {}
 
-    def load(self, episodes):
-        """Accept requests: generate every episode's message windows (stream id =
-        episode id) into one HBM payload buffer.  Returns its size in bytes."""
-        counts = np.array([e.n_steps * e.msgs_per_step for e in episodes], np.int64)
-        gen = self.lobgen.DeviceStreams(self.params, len(episodes),
-                                        stream_ids=[e.id for e in episodes])
-        self.d_msgs, off = gen.advance(counts)
-        off = off.cpu().numpy()
-        for e, b in zip(episodes, off[:-1]):
-            e.base = int(b)
-        torch.cuda.synchronize()
-        return int(counts.sum()) * MSG_BYTES
+    def footprint(self, ep):
+        return footprint_bytes(ep.capacity, self.tcap, ep.msgs_per_step)
 
     def _can_admit(self, ep):
         pool = self.pools.get(ep.capacity)
         if pool is None:
             raise ValueError("no pool for capacity %d" % ep.capacity)
-        return bool(pool.free) and self.used + self.fp[ep.capacity] <= self.budget
+        return bool(pool.free) and self.used + self.footprint(ep) <= self.budget
 
     def run(self, episodes, clock="wall", max_ticks=None):
         """Serve `episodes` (arrival in seconds for clock='wall', in ticks for
         clock='virtual'); returns a report dict."""
-        payload = self.load(episodes)
+        for ep in episodes:
+            if self.footprint(ep) > self.budget:
+                raise ValueError("episode %d alone exceeds the HBM budget" % ep.id)
         order = sorted(range(len(episodes)), key=lambda i: episodes[i].arrival)
         pending = collections.deque(order)
-        waiting = []
+        waiting = collections.deque()
         lat, weights, queue_len = [], [], []
+        finals = []  # (episode id, pool, slot, captured tensors)
         steps_done = msgs_done = 0
         max_active = max_used = 0
         tick = 0
@@ -225,12 +308,13 @@ class Server:
             now = (time.perf_counter() - t0) if clock == "wall" else float(tick)
             while pending and episodes[pending[0]].arrival <= now:
                 waiting.append(pending.popleft())
-            still = []
-            for i in waiting:  # first fit, in arrival order
+            # first fit, in arrival order
+            still = collections.deque()
+            for i in waiting:
                 ep = episodes[i]
                 if self._can_admit(ep):
                     self.pools[ep.capacity].admit(i, ep)
-                    self.used += self.fp[ep.capacity]
+                    self.used += self.footprint(ep)
                     ep.admitted = now
                 else:
                     still.append(i)
@@ -247,66 +331,71 @@ class Server:
                 continue
             if self.collect:
                 ts = time.perf_counter()
-                launched = [(p, *p.launch_step(self.d_msgs)) for p in busy]
+                launched = [(p, *p.launch_step()) for p in busy]
                 for p in busy:
                     p.stream.synchronize()
                 te = time.perf_counter()
                 lat.append(te - ts)
                 weights.append(active)
-            else:
-                # the host runs ahead; each pool's tick is timed on the GPU
-                te = time.perf_counter()
-                launched = [(p, *p.launch_step(self.d_msgs, timing=True)) for p in busy]
-            steps_done += active
-            msgs_done += sum(m for _, _, m, _ in launched)
-            if self.collect:
                 self._record(episodes, launched)
+            else:
+                te = time.perf_counter()
+                launched = [(p, *p.launch_step(timing=True)) for p in busy]
+            steps_done += active
+            msgs_done += sum(m for _, _, m in launched)
             now_after = (te - t0) if clock == "wall" else float(tick)
-            for p, act, _, _ in launched:
+            for p, act, _ in launched:
                 p.step[act] += 1
-                for s in act[p.step[act] >= p.n_steps[act]]:
+                ended = act[p.step[act] >= p.n_steps[act]]
+                if len(ended) and self.keep_final:
+                    cap = p.capture_final()
+                    for s in ended:
+                        finals.append((episodes[int(p.ep[s])].id, int(s), cap))
+                for s in ended:
                     ep = episodes[int(p.ep[s])]
-                    if self.collect:
-                        self._final_book(p, int(s), ep)
                     ep.done = now_after
                     p.ep[s] = -1
                     p.n_active -= 1
                     p.free.append(int(s))
-                    self.used -= self.fp[ep.capacity]
+                    self.used -= self.footprint(ep)
             tick += 1
             if max_ticks is not None and tick >= max_ticks:
                 break
         torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        gen_ms = []
         for p in self.pools.values():
             p.flush()
             for ms, n in p.lat:
                 lat.append(ms / 1e3)
                 weights.append(n)
-            p.lat = []
-        wall = time.perf_counter() - t0
+            gen_ms += p.gen_ms
+            p.lat, p.gen_ms = [], []
+        for eid, s, (bk, ctr) in finals:
+            self.final_books[eid] = {k: v[s].cpu().numpy().copy() for k, v in bk.items()}
+            self.final_counters[eid] = ctr[s].cpu().numpy().copy()
         lat_ms = np.repeat(np.asarray(lat) * 1e3, weights) if lat else np.zeros(1)
         waits = [e.admitted - e.arrival for e in episodes if not math.isnan(e.admitted)]
         return {"episodes": len(episodes), "episode_steps": steps_done, "messages": msgs_done,
-                "payload_bytes": payload, "wall_s": wall, "ticks": tick,
+                "wall_s": wall, "ticks": tick,
                 "steps_per_s": steps_done / wall, "msgs_per_s": msgs_done / wall,
                 "p50_step_ms": float(np.percentile(lat_ms, 50)),
                 "p99_step_ms": float(np.percentile(lat_ms, 99)),
+                "p50_window_gen_ms": float(np.percentile(gen_ms, 50)) if gen_ms else None,
                 "mean_batch": float(np.mean(weights)) if weights else 0.0,
                 "admission_wait_p50": float(np.percentile(waits, 50)) if waits else 0.0,
                 "admission_wait_p99": float(np.percentile(waits, 99)) if waits else 0.0,
                 "max_queue": max(q for _, q in queue_len) if queue_len else 0,
                 "max_active": max_active, "max_hbm_bytes_admitted": max_used,
+                "hbm_budget_bytes": self.budget,
+                "hbm_reserved_bytes": sum(p.reserved_bytes for p in self.pools.values()),
+                "slots": {c: p.slots for c, p in self.pools.items()},
                 "queue": queue_len}
 
     def _record(self, episodes, launched):
-        for p, act, _, _ in launched:
+        for p, act, _ in launched:
             lv = [x.cpu().numpy() for x in p.levels]
             tc = p.d_tcount.cpu().numpy()
             for s in act:
                 ep = episodes[int(p.ep[s])]
                 self.records[ep.id].append((tuple(x[s].tolist() for x in lv), int(tc[s])))
-
-    def _final_book(self, p, s, ep):
-        bk = p.engine.book()
-        p.stream.synchronize()
-        self.final_books[ep.id] = {k: v[s].cpu().numpy().copy() for k, v in bk.items()}

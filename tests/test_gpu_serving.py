@@ -1,9 +1,16 @@
 """Serving loop: continuous batching with admission by HBM footprint.
 
-Each episode's per-step outputs (top levels, trade counts) and final book are
-the same when it is served alone and inside a mix where others arrive, wait,
-run and leave around it (tolerance: exact, all outputs are integers); a subset
-is also replayed step by step through the CPU oracle."""
+Each episode's results are the same when it is served alone and inside a mix
+where others arrive, wait, run and leave around it (tolerance: exact, all
+outputs are integers).  Checked on both paths of the server: the synchronous
+one (every tick waited for; per-step levels and trade counts compared) and the
+asynchronous one the benchmark runs (the host runs up to RING ticks ahead,
+windows are produced on a second stream, staging buffers are reused), where
+every episode's final book and counters are compared.  A subset is replayed
+step by step through the CPU oracle.  Capacities 7, 100, 250 and 500 cover
+register-resident and grouped shared-memory books."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -12,57 +19,106 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
+CAPS = (7, 100, 250, 500)
+SEED = 77
 
-def _mix(n=36, seed=5):
+
+def _mix(n=40, seed=5, caps=CAPS):
     from paper_2308_13289_b300.serve import Episode
     rng = np.random.default_rng(seed)
     eps = []
     for i in range(n):
-        eps.append(Episode(id=1000 + i, capacity=int(rng.choice([7, 100, 250])),
+        eps.append(Episode(id=1000 + i, capacity=int(rng.choice(caps)),
                            n_steps=int(rng.integers(3, 21)), msgs_per_step=int(rng.integers(20, 61)),
                            arrival=float(rng.integers(0, 30))))
     return eps
 
 
 def _clone(eps):
-    import copy
     return [copy.copy(e) for e in eps]
+
+
+def _alone(ep):
+    from paper_2308_13289_b300.serve import Server
+    srv = Server(capacities=(ep.capacity,), trade_capacity=512, max_slots=1, collect=True,
+                 seed=SEED, msgs_per_step=(20, 60))
+    e1 = copy.copy(ep)
+    e1.arrival = 0.0
+    srv.run([e1], clock="virtual")
+    return srv
+
+
+def _oracle_episode(ep):
+    """The episode replayed step by step through the CPU oracle: per-step
+    (levels, trade count), final book, counters."""
+    params = lobgen.make_params(SEED, "pm1")
+    hs = lobgen.HostStreams(params, 1, stream_ids=[ep.id])
+    o = oracle.Oracle(1, ep.capacity, 512)
+    steps = []
+    for _ in range(ep.n_steps):
+        m, off = hs.advance([ep.msgs_per_step])
+        o.process(m, off)
+        steps.append((tuple(x[0].tolist() for x in o.levels(10)), int(o.trades()[1][0])))
+    return steps, {k: v[0] for k, v in o.book().items()}, o.counters()[0]
+
+
+def _pick(eps):
+    """Episodes of every capacity for the alone / oracle comparisons."""
+    out = []
+    for c in CAPS:
+        out += [e for e in eps if e.capacity == c][:3]
+    return out
 
 
 def test_alone_equals_mix_and_oracle():
     from paper_2308_13289_b300.serve import Server
     eps = _mix()
-    srv = Server(capacities=(7, 100, 250), trade_capacity=512, max_slots=6, collect=True,
-                 seed=77)
+    srv = Server(capacities=CAPS, trade_capacity=512, max_slots=6, collect=True, seed=SEED,
+                 msgs_per_step=(20, 60))
     rep = srv.run(_clone(eps), clock="virtual")
     assert rep["episode_steps"] == sum(e.n_steps for e in eps)
     assert rep["max_queue"] > 0, "the mix should make episodes wait for slots"
     assert rep["max_active"] > 6, "several capacity classes should run at once"
-    for ep in eps[:12]:
-        alone = Server(capacities=(ep.capacity,), trade_capacity=512, max_slots=1, collect=True,
-                       seed=77)
-        import copy
-        e1 = copy.copy(ep)
-        e1.arrival = 0.0
-        alone.run([e1], clock="virtual")
+    for ep in _pick(eps):
+        alone = _alone(ep)
         assert alone.records[ep.id] == srv.records[ep.id], ep.id
         for k, v in alone.final_books[ep.id].items():
             assert np.array_equal(v, srv.final_books[ep.id][k]), (ep.id, k)
-    # oracle replay of a few episodes, step by step
-    params = lobgen.make_params(77, "pm1")
-    for ep in eps[:8]:
-        hs = lobgen.HostStreams(params, 1, stream_ids=[ep.id])
-        o = oracle.Oracle(1, ep.capacity, 512)
-        for t in range(ep.n_steps):
-            m, off = hs.advance([ep.msgs_per_step])
-            o.process(m, off)
-            lv = o.levels(10)
-            got_lv, got_tc = srv.records[ep.id][t]
-            assert tuple(x[0].tolist() for x in lv) == got_lv, (ep.id, t)
-            assert int(o.trades()[1][0]) == got_tc
-        ob = o.book()
-        for k, v in ob.items():
-            assert np.array_equal(v[0], srv.final_books[ep.id][k]), (ep.id, k)
+        steps, book, ctr = _oracle_episode(ep)
+        assert srv.records[ep.id] == steps, ep.id
+        for k, v in book.items():
+            assert np.array_equal(v, srv.final_books[ep.id][k]), (ep.id, k)
+        assert np.array_equal(srv.final_counters[ep.id], ctr), ep.id
+
+
+def test_async_run_ahead_equals_alone_and_oracle():
+    """The benchmark's path: no tick is waited for, windows come from the
+    generator stream, slots are reused as soon as the host sees an episode
+    end.  Every episode's final book and counters equal the synchronous
+    alone run and the oracle."""
+    from paper_2308_13289_b300.serve import RING, Server
+    eps = _mix(48, seed=11)
+    srv = Server(capacities=CAPS, trade_capacity=512, max_slots=5, keep_final=True, seed=SEED,
+                 msgs_per_step=(20, 60))
+    rep = srv.run(_clone(eps), clock="virtual")
+    assert rep["episode_steps"] == sum(e.n_steps for e in eps)
+    assert rep["max_queue"] > 0 and rep["ticks"] > 2 * RING
+    assert rep["p50_window_gen_ms"] is not None
+    assert set(srv.final_books) == {e.id for e in eps}
+    by_id = {e.id: e for e in eps}
+    checked = 0
+    for ep in _pick(eps):
+        alone = _alone(ep)
+        for k, v in alone.final_books[ep.id].items():
+            assert np.array_equal(v, srv.final_books[ep.id][k]), (ep.id, k)
+        assert np.array_equal(alone.final_counters[ep.id], srv.final_counters[ep.id]), ep.id
+        checked += 1
+    assert checked >= 8
+    for eid in sorted(srv.final_books)[::4]:
+        _, book, ctr = _oracle_episode(by_id[eid])
+        for k, v in book.items():
+            assert np.array_equal(v, srv.final_books[eid][k]), (eid, k)
+        assert np.array_equal(srv.final_counters[eid], ctr), eid
 
 
 def test_process_segments_equals_process_batch():
@@ -85,13 +141,17 @@ def test_process_segments_equals_process_batch():
 
 
 def test_admission_respects_hbm_budget():
+    """Equal footprints: a budget of five episodes admits at most five at a
+    time, makes the others queue, and still serves every step."""
     from paper_2308_13289_b300.serve import Server, footprint_bytes
     eps = _mix(24, seed=9)
     for e in eps:
-        e.capacity = 100
-    fp = footprint_bytes(100, 256)
-    srv = Server(capacities=(100,), hbm_budget=5 * fp, trade_capacity=256, max_slots=64, seed=3)
+        e.capacity, e.msgs_per_step = 100, 40
+    fp = footprint_bytes(100, 256, 40)
+    srv = Server(capacities=(100,), hbm_budget=5 * fp, trade_capacity=256, max_slots=64, seed=3,
+                 msgs_per_step=(40, 40))
     rep = srv.run(eps, clock="virtual")
-    assert rep["max_active"] <= 5
-    assert rep["max_hbm_bytes_admitted"] <= 5 * fp
+    assert rep["max_active"] == 5
+    assert rep["max_hbm_bytes_admitted"] == 5 * fp
+    assert rep["max_queue"] > 0
     assert rep["episode_steps"] == sum(e.n_steps for e in eps)
