@@ -133,12 +133,16 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def measured_traffic():
-    """DRAM bytes (read + write) of one headline k_process launch from the
-    committed ncu capture, or None once the kernel sources have changed since
-    the counters were taken."""
+COUNTER_RECORD = os.path.join("profiles", "k_process_replay_1024x100k_counters.txt")
+
+
+def measured_counters():
+    """ncu counters of one headline k_process launch from the committed
+    record: DRAM bytes (read + write) and warp-instructions executed, with the
+    messages of that launch.  None once the kernel sources have changed since
+    the counters were taken (the record holds their hash)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_process_replay_1024x100k_traffic.txt")
+    path = os.path.join(ROOT, COUNTER_RECORD)
     try:
         kv = dict(line.split(":", 1) for line in open(path)
                   if ":" in line and not line.startswith("#"))
@@ -148,9 +152,29 @@ def measured_traffic():
                 h.update(f.read())
         if h.hexdigest() != kv["sources_sha256"].strip():
             return None
-        return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
+        return {"dram_bytes": int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"]),
+                "inst_executed": int(kv["smsp_inst_executed"]),
+                "messages": int(kv["messages"])}
     except (OSError, KeyError, ValueError):
         return None
+
+
+def issue_roofline(inst_per_msg, msgs_per_s, sm_mhz, source, sms=None):
+    """Fraction of the GPU's instruction-issue capacity a kernel uses: warp-
+    instructions per message x messages per second, over (SMs x 4 schedulers,
+    one warp-instruction per cycle each, x the median SM clock sampled during
+    the timed region)."""
+    if sms is None:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    if inst_per_msg is None or not sm_mhz:
+        return {"bound": "issue", "inst_per_msg": inst_per_msg, "frac": None, "source": source}
+    achieved = inst_per_msg * msgs_per_s
+    peak = sms * 4 * sm_mhz * 1e6
+    return {"bound": "issue", "inst_per_msg": round(inst_per_msg, 2),
+            "achieved": round(achieved / 1e9, 2), "peak": round(peak / 1e9, 2),
+            "unit": "G warp-instructions/s", "frac": round(achieved / peak, 4),
+            "sms": sms, "sm_mhz": sm_mhz, "source": source}
 
 
 def workload_streams(name, rank):
@@ -373,13 +397,20 @@ def run_engine(args):
     state_bytes = 2 * n * eng_book_bytes(cap)
     alg_bytes = 32 * total_msgs + 32 * trades_per_step + state_bytes + 8 * (n + 1)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
-    traffic = (measured_traffic() if args.workload == "replay_1024x100k" and cap == 100
-               else None)
+    counters = (measured_counters() if args.workload == "replay_1024x100k" and cap == 100
+                and not args.launch else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 5), "traffic": traffic,
+            "frac": round(achieved / peak, 5),
+            "traffic": counters["dram_bytes"] if counters else None,
             "kernel": "k_process<%d>" % (eng_book_bytes(cap) // (48 * 32)),
             "kernel_ms": round(kernel_ms, 4), "algorithmic_bytes_per_launch": int(alg_bytes),
             "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+    # the roofline that binds this kernel: instruction issue of each book's
+    # serial chain (warp-instructions per message from the committed ncu record)
+    ipm = counters["inst_executed"] / counters["messages"] if counters else None
+    roof["issue"] = issue_roofline(ipm, total_msgs / (kernel_ms / 1e3), clk.get("sm_mhz"),
+                                   COUNTER_RECORD + " (smsp__inst_executed.sum)" if counters
+                                   else "no counter record for these kernel sources")
 
     extras = None
     if not args.no_extras and args.workload == "replay_1024x100k":
@@ -387,7 +418,8 @@ def run_engine(args):
         del d_msgs
         torch.cuda.empty_cache()
         extras = {}
-        for key, fn in (("uneven_4096_lognormal", run_uneven), ("rl_exec_8192x400", run_rl),
+        for key, fn in (("replay_book_sweep", lambda a, r: run_sweep(a, r, ipm, clk)),
+                        ("uneven_4096_lognormal", run_uneven), ("rl_exec_8192x400", run_rl),
                         ("serving_mix", run_serving), ("ablation_paper_literal", run_ablation)):
             with nvtx(key):
                 extras[key] = fn(args, rank)
@@ -419,6 +451,74 @@ def run_engine(args):
 def _events():
     import torch
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_sweep(args, rank, inst_per_msg=None, clk=None, sizes=(1024, 4096, 16384), per=10_000):
+    """The replay workload's generator at 10^4 messages per book and a growing
+    number of books (persistent form, autotuned shape): where the kernel
+    leaves the regime in which each book's serial chain sets the time, and
+    how the HBM and issue fractions move."""
+    import torch
+
+    import lobgen
+    import oracle
+    import paper_2308_13289_b300 as eng
+    from paper_2308_13289_b300 import autotune
+    w = lobgen.WORKLOADS["replay_1024x10k"]
+    cap = w["capacity"]
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    peak, peak_kind = measured_peaks()
+    res = {"messages_per_book": per, "capacity": cap, "seed": w["seed"],
+           "peak_hbm_gbs": peak, "inst_per_msg_source": "headline ncu record"}
+    for n in sizes:
+        ids = np.arange(rank * n, (rank + 1) * n, dtype=np.uint64)
+        gen = lobgen.DeviceStreams(params, n, stream_ids=ids)
+        dm, doff = gen.advance([per] * n)
+        del gen
+        tcap = per // 2 + 1024
+        e = eng.Engine(n, cap, tcap)
+        pre_n = 2000
+        pre = dm.view(n, per, 8)[:, :pre_n].contiguous().view(-1, 8)
+        pre_off = torch.arange(0, n * pre_n + 1, pre_n, dtype=torch.int64, device="cuda")
+        shape = autotune.tune(n, cap, pre, pre_off, trade_capacity=pre_n, mean_msgs=per)
+        autotune.apply(e, shape)
+        del pre, pre_off
+        times = []
+        for i in range(args.warmup + args.steps):
+            e.reset()
+            a, b = _events()
+            a.record()
+            e.process_batch(dm, doff)
+            b.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                times.append(a.elapsed_time(b))
+        ms = float(np.mean(times))
+        ctr, st = e.stats()
+        trades = int(ctr[:, 6].sum().item())
+        total = n * per
+        alg = 32 * total + 32 * trades + 2 * n * eng_book_bytes(cap) + 8 * (n + 1)
+        rate = total / ms * 1e3
+        row = {"n_books": n, "ms_per_step": round(ms, 4), "msgs_per_s": round(rate, 1),
+               "launch": {"warps_per_cta": shape["warps"], "chunk_msgs": shape["chunk"]},
+               "hbm_frac": round(alg / (ms / 1e3) / 1e9 / peak, 5),
+               "issue": issue_roofline(inst_per_msg, rate, (clk or {}).get("sm_mhz"),
+                                       "headline record's instructions per message"),
+               "device_status": int(st.item())}
+        if rank == 0:
+            sample = np.array([0, n // 3, n - 1])
+            hm, hoff = lobgen.generate(params, [per] * len(sample), stream_ids=ids[sample])
+            o = oracle.Oracle(len(sample), cap, tcap)
+            o.process(hm, hoff)
+            bk = e.book()
+            ok = all(np.array_equal(bk[k][sample].cpu().numpy(), v) for k, v in o.book().items())
+            ok &= np.array_equal(ctr[sample].cpu().numpy(), o.counters())
+            row["parity"] = {"books_checked": int(len(sample)), "bit_exact": bool(ok)}
+        res["n%d" % n] = row
+        e.close()
+        del dm, doff
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_ablation(args, rank, name="replay_1024x10k"):
@@ -847,21 +947,8 @@ def cpu_baseline_and_parity(e, msgs, off, counts, cap, tcap, depth, n_sample, w)
     dt = time.perf_counter() - t
     n_msgs = int(sub_off[-1])
     cpu = {"value": round(n_msgs / dt, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
-           "sample": "first %d of %d books, full %s-message streams (%d messages), "
-                     "std::map oracle, one std::thread per core"
-                     % (n_sample, len(counts), "{:,}".format(int(counts[0])) if
-                        (counts == counts[0]).all() else "lognormal", n_msgs),
-           "seconds": round(dt, 3), "cpu_model": cpu_model()}
-    # the same oracle on one thread, over the first 16 books
-    n1 = min(16, n_sample)
-    o1 = oracle.Oracle(n1, cap, tcap)
-    t = time.perf_counter()
-    o1.process(msgs[:int(off[n1])], off[:n1 + 1], threads=1)
-    dt1 = time.perf_counter() - t
-    cpu["single_thread"] = {"value": round(int(off[n1]) / dt1, 1), "unit": UNIT,
-                            "sample": "first %d books, full streams (%d messages)"
-                                      % (n1, int(off[n1])), "seconds": round(dt1, 3)}
-    del o1
+           "sample": oracle_sample_text(n_sample, counts, n_msgs), "seconds": round(dt, 3),
+           "cpu_model": cpu_model(), "single_thread": oracle_single_thread(msgs, off, cap, tcap)}
     # parity
     bk = e.book()
     gl = e.levels(depth)
@@ -883,6 +970,26 @@ def cpu_baseline_and_parity(e, msgs, off, counts, cap, tcap, depth, n_sample, w)
     return cpu, parity
 
 
+def oracle_sample_text(n_sample, counts, n_msgs):
+    return ("first %d of %d books, full %s-message streams (%d messages), std::map oracle, "
+            "one std::thread per host core" % (
+                n_sample, len(counts), "{:,}".format(int(counts[0])) if (counts == counts[0]).all()
+                else "lognormal", n_msgs))
+
+
+def oracle_single_thread(msgs, off, cap, tcap, n1=16):
+    """The oracle on one thread over the first n1 books' full streams."""
+    import oracle
+    n1 = min(n1, len(off) - 1)
+    o1 = oracle.Oracle(n1, cap, tcap)
+    t = time.perf_counter()
+    o1.process(msgs[:int(off[n1])], off[:n1 + 1], threads=1)
+    dt1 = time.perf_counter() - t
+    return {"value": round(int(off[n1]) / dt1, 1), "unit": UNIT,
+            "sample": "first %d books, full streams (%d messages), 1 thread" % (n1, int(off[n1])),
+            "seconds": round(dt1, 3)}
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -896,14 +1003,16 @@ def cpu_model():
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args):
-    """The CPU oracle, as it stands, on the host cores: each step processes a
-    bounded sample (the first 64 books' full streams) of the same workload."""
+    """The CPU oracle, as it stands, on the host cores: each step processes the
+    same bounded sample as the engine arm's cpu_baseline (the first
+    --oracle-books books' full streams, all host threads), and the
+    single-thread figure is measured the same way too."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     w, params, counts, msgs, off, sid = workload_streams(args.workload, 0)
-    n_sample = min(64, len(counts))
+    n_sample = min(max(1, args.oracle_books), len(counts))
     sub_off = off[:n_sample + 1]
     sub = msgs[:int(sub_off[-1])]
     cap, tcap = args.capacity or w["capacity"], trade_capacity_for(counts)
@@ -922,16 +1031,17 @@ def run_reference(args):
         step()
     dt = (time.perf_counter() - t) / args.steps
     value = n_msgs / dt
-    sample = "first %d of %d books, full streams (%d messages) per step" % (
-        n_sample, len(counts), n_msgs)
+    cpu = {"value": round(value, 1), "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": oracle_sample_text(n_sample, counts, n_msgs) + " per step",
+           "cpu_model": cpu_model(),
+           "single_thread": oracle_single_thread(msgs, off, cap, tcap)}
     line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": DATA, "impl": "reference",
             "config": {"workload": args.workload, "n_books_per_gpu": len(counts),
                        "capacity": cap, "form": "cpu oracle sample"},
-            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": threads,
-                             "kind": "oracle", "sample": sample, "cpu_model": cpu_model()},
+            "cpu_baseline": cpu,
             "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

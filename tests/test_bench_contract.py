@@ -35,6 +35,9 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert "sample" in cb
+    # the same sample as the engine arm's cpu_baseline (256 books by default)
+    assert cb["sample"].startswith("first 256 of 1024 books")
+    assert cb["single_thread"]["value"] > 0 and "1 thread" in cb["single_thread"]["sample"]
     assert d["config"]["workload"] == "replay_1024x10k" and d["config"]["capacity"] == 100
 
 
@@ -50,3 +53,15 @@ def test_book_bytes_follow_the_slot_count(cap, slots):
     import bench
     # a book is two sides of 32*K slots, 24 bytes a slot (px, qty, oid, tid, time)
     assert bench.eng_book_bytes(cap) == 2 * slots * 24
+
+
+def test_issue_roofline_arithmetic():
+    sys.path.insert(0, ROOT)
+    import bench
+    # 118 warp-instructions per message at 3.89e9 messages/s on 148 SMs at
+    # 2,032 MHz: 4.59e11 of 1.203e12 warp-instructions/s
+    r = bench.issue_roofline(118.0, 3.89e9, 2032.0, "test", sms=148)
+    assert r["bound"] == "issue"
+    assert abs(r["frac"] - 118.0 * 3.89e9 / (148 * 4 * 2032e6)) < 1e-4
+    assert abs(r["peak"] - 148 * 4 * 2.032) < 0.01
+    assert bench.issue_roofline(None, 1.0, 2032.0, "none", sms=148)["frac"] is None

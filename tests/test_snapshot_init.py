@@ -300,8 +300,10 @@ def test_gpu_init_from_levels_matches_oracle(cap, depth):
     o = oracle.Oracle(n_books, cap, 16)
     emptied = o.init_from_levels(bp, bq, ap, aq, time_ns=123456789)
     ref = oracle_outputs(o)
-    assert_same(g, ref)
+    # some sides are listed out of priority order: loaded empty and flagged
     assert emptied > 0
+    ref["status"] = eng.STATUS_BAD_BOOK_LOAD
+    assert_same(g, ref)
     assert int(st.item()) == eng.STATUS_BAD_BOOK_LOAD
 
 
