@@ -398,7 +398,7 @@ def run_engine(args):
     alg_bytes = 32 * total_msgs + 32 * trades_per_step + state_bytes + 8 * (n + 1)
     achieved = alg_bytes / (kernel_ms / 1e3) / 1e9
     counters = (measured_counters() if args.workload == "replay_1024x100k" and cap == 100
-                and not args.launch else None)
+                else None)
     roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 5),
             "traffic": counters["dram_bytes"] if counters else None,

@@ -209,11 +209,13 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
 
 // ---------------------------------------------------------------- primitives
 
-// Shift slots [p, n_after) right by one and place `val` at slot p, with the
+// Shift the slots from p on right by one and place `val` at slot p, with the
 // left neighbour's last slot already fetched (prev = __shfl_up_sync(kFull,
-// v[K - 1], 1)), so that the shuffle can be issued before p is known.
+// v[K - 1], 1)), so that the shuffle can be issued before p is known.  Slots
+// at or past the new count hold no order and every reader bounds its slots by
+// the count, so they take whatever the shift brings (no upper bound to test).
 template <int K, typename T>
-__device__ __forceinline__ void shift_in_prev(T (&v)[K], int p, int n_after, T val, T prev)
+__device__ __forceinline__ void shift_in_prev(T (&v)[K], int p, T val, T prev)
 {
     const int l = lane_id();
     T nv[K];
@@ -221,16 +223,17 @@ __device__ __forceinline__ void shift_in_prev(T (&v)[K], int p, int n_after, T v
     for (int j = 0; j < K; ++j) {
         const int s = l * K + j;
         T left = (j == 0) ? prev : v[j - 1];
-        nv[j] = (s == p) ? val : ((s > p && s < n_after) ? left : v[j]);
+        nv[j] = (s == p) ? val : ((s > p) ? left : v[j]);
     }
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = nv[j];
 }
 
 // shift_out with the right neighbour's first slot already fetched
-// (next = __shfl_down_sync(kFull, v[0], 1)).
+// (next = __shfl_down_sync(kFull, v[0], 1)); slots past the new count take
+// whatever the shift brings, as in shift_in_prev.
 template <int K, typename T>
-__device__ __forceinline__ void shift_out_next(T (&v)[K], int p, int n, T next)
+__device__ __forceinline__ void shift_out_next(T (&v)[K], int p, T next)
 {
     const int l = lane_id();
     T nv[K];
@@ -238,7 +241,7 @@ __device__ __forceinline__ void shift_out_next(T (&v)[K], int p, int n, T next)
     for (int j = 0; j < K; ++j) {
         const int s = l * K + j;
         T right = (j == K - 1) ? next : v[j + 1];
-        nv[j] = (s >= p && s < n - 1) ? right : v[j];
+        nv[j] = (s >= p) ? right : v[j];
     }
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = nv[j];
@@ -565,12 +568,12 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
         ctr.evicted_qty += slot_value<K>(v.q, cap - 1);
     }
     const int n_after = full ? cap : n + 1;
-    shift_in_prev<K>(v.px, p, n_after, P, pv_px);
-    shift_in_prev<K>(v.q, p, n_after, Q, pv_q);
-    shift_in_prev<K>(v.oid, p, n_after, oid, pv_oid);
-    shift_in_prev<K>(v.tid, p, n_after, tid, pv_tid);
-    shift_in_prev<K>(v.tlo, p, n_after, tlo, pv_tlo);
-    shift_in_prev<K>(v.thi, p, n_after, thi, pv_thi);
+    shift_in_prev<K>(v.px, p, P, pv_px);
+    shift_in_prev<K>(v.q, p, Q, pv_q);
+    shift_in_prev<K>(v.oid, p, oid, pv_oid);
+    shift_in_prev<K>(v.tid, p, tid, pv_tid);
+    shift_in_prev<K>(v.tlo, p, tlo, pv_tlo);
+    shift_in_prev<K>(v.thi, p, thi, pv_thi);
     bk.template release<X>(v, lane_touches<K>(p, n_after));
     if (p == 0) bk.template set_best<X>(P);
     n = n_after;
@@ -625,12 +628,12 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
     const int32_t nx_tid = __shfl_down_sync(kFull, v.tid[0], 1);
     const int32_t nx_tlo = __shfl_down_sync(kFull, v.tlo[0], 1);
     const int32_t nx_thi = __shfl_down_sync(kFull, v.thi[0], 1);
-    shift_out_next<K>(v.px, p, n, nx_px);
-    shift_out_next<K>(v.q, p, n, nx_q);
-    shift_out_next<K>(v.oid, p, n, nx_oid);
-    shift_out_next<K>(v.tid, p, n, nx_tid);
-    shift_out_next<K>(v.tlo, p, n, nx_tlo);
-    shift_out_next<K>(v.thi, p, n, nx_thi);
+    shift_out_next<K>(v.px, p, nx_px);
+    shift_out_next<K>(v.q, p, nx_q);
+    shift_out_next<K>(v.oid, p, nx_oid);
+    shift_out_next<K>(v.tid, p, nx_tid);
+    shift_out_next<K>(v.tlo, p, nx_tlo);
+    shift_out_next<K>(v.thi, p, nx_thi);
     bk.template release<X>(v, lane_touches<K>(p, n - 1));
     bk.template refresh_best<X>();
     n -= 1;
