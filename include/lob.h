@@ -343,6 +343,10 @@ int lob_env_reset(lob_env* env, void* stream);
 
 /* Run steps step0 .. step0+n_run-1 of every environment in ONE launch (the
  * books stay in on-chip memory across the steps).  n_run = 1 is one step.
+ * When there are more environments than resident warps, each environment's
+ * steps are split into segments that the persistent grid hands out one after
+ * another (a segment resumes from what the previous one wrote back); the
+ * results do not depend on it (lob_env_segments).
  *   d_replay : data messages, 16-byte aligned; env b's step t window is
  *              d_replay[b*stride_env + t*msgs_per_step ..][0 .. msgs_per_step)
  *   d_draws  : uint32[n_run][n_books] agent draws of those steps, or NULL
@@ -362,6 +366,13 @@ int lob_env_run(lob_env* env, const lob_msg_t* d_replay, int64_t stride_env, int
                 int32_t n_run, const uint32_t* d_draws, const float* d_actions, float* d_reward,
                 int32_t* d_bid_px, int32_t* d_bid_qty, int32_t* d_ask_px, int32_t* d_ask_qty,
                 int64_t* d_fills, int32_t* d_l1, void* stream);
+
+/* No counterpart in the paper (introspection for tests and tuning): how many
+ * segments of consecutive steps each environment's run was split into by the
+ * most recent lob_env_run (1 = whole runs; the persistent grid hands out
+ * segments, not whole episodes, when there are more environments than
+ * resident warps), or -1 for a NULL env. */
+int32_t lob_env_segments(const lob_env* env);
 
 /* Observation of every environment after its most recent step (Sec. 5.2.2):
  * d_obs float [n_books][6M + 8], M = msgs_per_step, laid out in the order the

@@ -218,6 +218,10 @@ def lob_env_observe(e, replay, stride_env, l1, obs, stream=None):
                                 _stream(stream)), "lob_env_observe")
 
 
+def lob_env_segments(e):
+    return int(lib().lob_env_segments(e))
+
+
 def lob_env_get_state(e, state, p_init, stream=None):
     check(lib().lob_env_get_state(e, _ptr(state), _ptr(p_init), _stream(stream)),
           "lob_env_get_state")
@@ -405,6 +409,10 @@ class Env:
                               device="cuda")
         lob_env_observe(self.h, replay, stride_env, l1, obs, self.stream)
         return obs
+
+    def segments(self):
+        """Segments per environment of the most recent run (lob_env_segments)."""
+        return lob_env_segments(self.h)
 
     def state(self):
         st = torch.empty((self.n, 5), dtype=torch.int64, device="cuda")

@@ -54,6 +54,7 @@ SIGNATURES = {
     "lob_selftest_wait": (ctypes.c_int, [i64, vp, vp, vp]),
     "lob_literal_process": (ctypes.c_int, [vp, vp, i32, i32, i32, i32, i32] + [vp] * 8 + [vp]),
     "lob_env_get_state": (ctypes.c_int, [vp, vp, vp, vp]),
+    "lob_env_segments": (ctypes.c_int32, [vp]),
     "lob_last_error": (ctypes.c_char_p, []),
     "lob_abi_version": (ctypes.c_int, []),
 }

@@ -29,11 +29,14 @@ struct lob_env {
     lob_ctx* book = nullptr;
     lob_env_config_t cfg;
     EnvStateDev* d_state = nullptr;
+    int64_t* d_seg_flag = nullptr;  // per environment: last segment finished (see k_env)
     int chunk = 0;        // staged messages per step (msgs_per_step rounded up to 8)
     int warps = 4;
-    int per_sm_v[4] = {1, 1, 1, 1};  // resident CTAs per SM of each (trace, snap) variant
+    int per_sm_v[8] = {1, 1, 1, 1, 1, 1, 1, 1};  // resident CTAs per SM of each
+                                                // (trace, snap, segmented) variant
     int smem_per_cta = 0;
     int64_t launches = 0;
+    int32_t last_segments = 0;  // segments per environment of the last lob_env_run
 };
 
 namespace {
@@ -65,7 +68,29 @@ struct EnvArgs {
     int32_t* l1;  // [n_run][n_envs][msgs_per_step][4] or null
     const float* actions;  // [n_run][n_envs][4] policy sizes, or null (stand-in draws)
     int32_t passive_ticks, tick;
+    int32_t n_seg, pad2_;  // segments each environment's steps are split into (1 = whole run)
+    int64_t* seg_flag;     // [n_envs] (epoch << 8) | segments of this launch finished
 };
+
+// Acquire load / release store of a 64-bit flag in global memory (gpu scope).
+__device__ __forceinline__ int64_t ld_acquire_gpu(const int64_t* p)
+{
+    int64_t v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int64_t* p, int64_t v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// order this thread's generic-proxy view of global memory before its later
+// async-proxy (bulk copy) reads of it
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 template <int K>
 __host__ __device__ constexpr int env_warp_smem(int chunk)
@@ -77,12 +102,22 @@ __host__ __device__ constexpr int env_warp_smem(int chunk)
 // kTrace: the kernel also writes the level-1 state after every data message;
 // kSnap: the snapshot cancel rule (LOB_FLAG_SNAPSHOT_CANCELS).  Separate
 // instantiations, so the default loop carries neither.
+// Work items: in the kSeg instantiation (n_seg > 1) every environment's run
+// is split into n_seg
+// segments of consecutive steps, handed out segment by segment over all
+// environments (item = segment * n_envs + env), so that the last round of a
+// persistent grid is not left with a few whole episodes while the other
+// warps idle.  A segment starts from the book, counts and agent state the
+// previous segment of its environment wrote back; it waits (bounded) on that
+// environment's flag, which the previous segment releases with the launch's
+// epoch, a device counter that every launch advances when its last warp
+// leaves (so a replayed CUDA graph never reads a stale flag).
 // Register-resident books (K <= 4) run in CTAs of four warps, bounded so that
 // three CTAs fit an SM (at most 168 registers a thread, no spills): twelve
 // environments' serial chains per SM instead of the eight that 186 registers
 // allowed, 20 % less time per episode.  (CTAs of one or two warps measured
 // no faster at 186 registers, and slower at 144-152 with 13-14 per SM.)
-template <int K, bool kTrace, bool kSnap>
+template <int K, bool kTrace, bool kSnap, bool kSeg>
 __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvArgs a)
 {
     using Book = typename BookPolicy<K>::type;
@@ -111,26 +146,68 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
 
     uint32_t g = 0;
     bool failed = false;
+    const int64_t epoch = kSeg ? (int64_t)*reinterpret_cast<volatile int32_t*>(&a.queue[2]) : 0;
     while (!failed) {
         int item = 0;
         if (l == 0) item = atomicAdd(&a.queue[0], 1);
         item = __shfl_sync(kFull, item, 0);
-        if (item >= a.n_envs) break;
-        const int b = item;
+        if (item >= a.n_envs * a.n_seg) break;
+        constexpr bool segmented = kSeg;
+        int seg = 0, b = item, r0 = 0, r1 = a.n_run;
+        if (segmented) {  // (n_run * n_seg < 2^31, checked on the host)
+            seg = item / a.n_envs;
+            b = item - seg * a.n_envs;
+            r0 = seg * a.n_run / a.n_seg;
+            r1 = (seg + 1) * a.n_run / a.n_seg;
+        }
         char* gbook = a.state + (int64_t)b * Geo<K>::BOOK_BYTES;
         const Msg* my = a.replay + (int64_t)b * a.stride_env;
+        if (segmented && seg > 0) {
+            // the previous segment of this environment must have written back
+            bool ok = true;
+            if (l == 0) {
+                const int64_t want = (epoch << 8) | seg;
+                if (ld_acquire_gpu(&a.seg_flag[b]) != want) {
+                    const uint64_t t0 = global_ns();
+                    while (ld_acquire_gpu(&a.seg_flag[b]) != want) {
+                        if (global_ns() - t0 > a.wait_ns) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                if (ok) fence_proxy_async_global();
+                else atomicOr(a.status, LOB_STATUS_TIMEOUT);
+            }
+            if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) continue;  // skip it (status set)
+        }
         if (l == 0) {
             fence_proxy_async();
-            for (int c = 0; c < 2 && c < a.n_run; ++c) {
+            for (int c = 0; c < 2 && c < r1 - r0; ++c) {
                 const uint32_t st = (g + c) & 1;
                 mbar_expect_tx(&bar[st], bytes + (c == 0 ? Geo<K>::BOOK_BYTES : 0));
                 if (c == 0) bulk_g2s(image, gbook, Geo<K>::BOOK_BYTES, &bar[st]);
                 bulk_g2s(msgbuf + st * chunk * 32,
-                         my + (int64_t)(a.step0 + c) * a.msgs_per_step, bytes, &bar[st]);
+                         my + (int64_t)(a.step0 + r0 + c) * a.msgs_per_step, bytes, &bar[st]);
             }
         }
-        int n_bid = a.counts[2 * b], n_ask = a.counts[2 * b + 1];
-        EnvStateDev es = a.env[b];
+        int n_bid, n_ask;
+        EnvStateDev es;
+        if (segmented) {
+            // written by another SM in this launch: read through L2, never a
+            // stale line of this SM's L1
+            n_bid = __ldcg(&a.counts[2 * b]);
+            n_ask = __ldcg(&a.counts[2 * b + 1]);
+            const int64_t* src = reinterpret_cast<const int64_t*>(&a.env[b]);
+            int64_t w[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) w[k] = __ldcg(src + k);
+            memcpy(&es, w, sizeof(es));
+        } else {
+            n_bid = a.counts[2 * b];
+            n_ask = a.counts[2 * b + 1];
+            es = a.env[b];
+        }
         Counters ctr{0, l};
         Tally tally;
         Book bk;
@@ -139,18 +216,19 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
         int64_t q_limit = 0, q_market = 0, n_msgs = 0;
         int64_t n_trades = 0, n_dropped = 0;
         TradeSink ts{a.trades + (int64_t)b * a.trade_cap, 0, a.trade_cap};
-        for (int r = 0; r < a.n_run; ++r) {
+        for (int r = r0; r < r1; ++r) {
             const int t = a.step0 + r;
-            const uint32_t st = (g + r) & 1, par = ((g + r) >> 1) & 1;
+            const int rr = r - r0;  // step within this work item
+            const uint32_t st = (g + rr) & 1, par = ((g + rr) >> 1) & 1;
             if (!mbar_wait_bounded(&bar[st], par, a.wait_ns)) {
                 if (l == 0) atomicOr(a.status, LOB_STATUS_TIMEOUT);
-                const int last = min(r + 1, a.n_run - 1);
-                for (int d = r; d <= last; ++d)
+                const int last = min(rr + 1, r1 - r0 - 1);
+                for (int d = rr; d <= last; ++d)
                     mbar_wait_bounded(&bar[(g + d) & 1], ((g + d) >> 1) & 1, a.wait_ns);
                 failed = true;
                 break;
             }
-            if (r == 0) bk.from_image(image);
+            if (rr == 0) bk.from_image(image);
             int4* mb = reinterpret_cast<int4*>(msgbuf + st * chunk * 32);
             const int cnt = a.msgs_per_step;
             for (int i = l; i < cnt; i += 32) {
@@ -357,7 +435,7 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
                                a.ask_qty + o * a.depth);
             }
             __syncwarp();
-            if (r + 2 < a.n_run && l == 0) {
+            if (r + 2 < r1 && l == 0) {
                 fence_proxy_async();
                 mbar_expect_tx(&bar[st], bytes);
                 bulk_g2s(msgbuf + st * chunk * 32, my + (int64_t)(t + 2) * a.msgs_per_step, bytes,
@@ -365,7 +443,7 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
             }
         }
         if (failed) break;
-        g += (uint32_t)a.n_run;
+        g += (uint32_t)(r1 - r0);
         bk.to_image(image);
         __syncwarp();
         const int4* src = reinterpret_cast<const int4*>(image);
@@ -395,12 +473,25 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
         const int64_t n_cancel = __shfl_sync(kFull, ctr.v, CTR_CANCEL);
         const int64_t n_hit = __shfl_sync(kFull, ctr.v, CTR_CANCEL_HIT);
         ctr.add(CTR_CANCEL_MISS, n_cancel - n_hit);
-        if (l < kNumCtr) a.stats[(int64_t)b * kNumCtr + l] += ctr.v;
+        // counters of consecutive segments may be added on different SMs: in L2
+        if (l < kNumCtr) {
+            int64_t* dst = &a.stats[(int64_t)b * kNumCtr + l];
+            if (segmented)
+                atomicAdd(reinterpret_cast<unsigned long long*>(dst), (unsigned long long)ctr.v);
+            else
+                *dst += ctr.v;
+        }
         if (l == 0) {
             a.counts[2 * b] = n_bid;
             a.counts[2 * b + 1] = n_ask;
             a.tcounts[b] = ts.count;
             a.env[b] = es;
+        }
+        if (segmented) {
+            // release this segment: every lane's write-back first
+            __threadfence();
+            __syncwarp();
+            if (l == 0) st_release_gpu(&a.seg_flag[b], (epoch << 8) | (seg + 1));
         }
         __syncwarp();
     }
@@ -410,6 +501,7 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
         if (done == total_warps - 1) {
             a.queue[0] = 0;
             a.queue[1] = 0;
+            if (kSeg) a.queue[2] += 1;  // the next segmented launch's epoch
             __threadfence();
         }
     }
@@ -461,13 +553,39 @@ __global__ void k_env_observe(const EnvStateDev* __restrict__ env, const Msg* __
     }
 }
 
-const void* env_kernel(int K, bool trace, bool snap)
+// Segments per environment for a launch of n_run steps on `warps` resident
+// warps: the split whose rounds of equal segments, ceil(n_envs*S/warps)/S
+// whole runs, finish first; 1 when every environment has a warp to itself,
+// and never segments shorter than 8 steps.
+int env_segments(int n_envs, int n_run, int warps)
 {
-#define LOB_ENV_K(k)                                                                   \
-    return trace ? (snap ? reinterpret_cast<const void*>(&k_env<k, true, true>)         \
-                         : reinterpret_cast<const void*>(&k_env<k, true, false>))       \
-                 : (snap ? reinterpret_cast<const void*>(&k_env<k, false, true>)        \
-                         : reinterpret_cast<const void*>(&k_env<k, false, false>))
+    if (warps < 1 || n_envs <= warps || n_run < 16 || n_envs > (1 << 26) || n_run > (1 << 26))
+        return 1;
+    int best = 1;
+    double best_cost = (double)((n_envs + warps - 1) / warps);
+    for (int S = 2; S <= 16 && n_run / S >= 8; ++S) {
+        const double cost = (double)(((int64_t)n_envs * S + warps - 1) / warps) / S;
+        if (cost < best_cost * 0.99) {
+            best = S;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
+const void* env_kernel(int K, bool trace, bool snap, bool seg)
+{
+#define LOB_ENV_KS(k, sg)                                                                  \
+    return trace ? (snap ? reinterpret_cast<const void*>(&k_env<k, true, true, sg>)         \
+                         : reinterpret_cast<const void*>(&k_env<k, true, false, sg>))       \
+                 : (snap ? reinterpret_cast<const void*>(&k_env<k, false, true, sg>)        \
+                         : reinterpret_cast<const void*>(&k_env<k, false, false, sg>))
+#define LOB_ENV_K(k)          \
+    if (seg) {                \
+        LOB_ENV_KS(k, true);  \
+    } else {                  \
+        LOB_ENV_KS(k, false); \
+    }
     switch (K) {
     case 1: LOB_ENV_K(1);
     case 2: LOB_ENV_K(2);
@@ -476,6 +594,7 @@ const void* env_kernel(int K, bool trace, bool snap)
     default: LOB_ENV_K(16);
     }
 #undef LOB_ENV_K
+#undef LOB_ENV_KS
 }
 
 int env_smem(int K, int chunk)
@@ -550,8 +669,8 @@ int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, vo
                       cfg->msgs_per_step);
         return LOB_E_INVAL;
     }
-    for (int v = 0; v < 4 && err == cudaSuccess; ++v) {
-        const void* fn = env_kernel(K, (v & 1) != 0, (v & 2) != 0);
+    for (int v = 0; v < 8 && err == cudaSuccess; ++v) {
+        const void* fn = env_kernel(K, (v & 1) != 0, (v & 2) != 0, (v & 4) != 0);
         err = lob_raise_smem_limit(fn, e->smem_per_cta);
         if (err == cudaSuccess)
             err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e->per_sm_v[v], fn,
@@ -560,6 +679,11 @@ int lob_env_create(lob_env** out, lob_ctx* book, const lob_env_config_t* cfg, vo
     }
     if (err == cudaSuccess)
         err = cudaMalloc(&e->d_state, sizeof(EnvStateDev) * (size_t)book->cfg.n_books);
+    if (err == cudaSuccess)
+        err = cudaMalloc(&e->d_seg_flag, sizeof(int64_t) * (size_t)book->cfg.n_books);
+    if (err == cudaSuccess)
+        err = cudaMemsetAsync(e->d_seg_flag, 0, sizeof(int64_t) * (size_t)book->cfg.n_books,
+                              (cudaStream_t)stream);
     if (err != cudaSuccess) {
         delete e;
         return lob_cuda_fail(err, "lob_env_create");
@@ -580,6 +704,10 @@ int lob_env_destroy(lob_env* e)
     if (e->d_state) {
         err = cudaDeviceSynchronize();
         cudaError_t e2 = cudaFree(e->d_state);
+        if (err == cudaSuccess) err = e2;
+    }
+    if (e->d_seg_flag) {
+        cudaError_t e2 = cudaFree(e->d_seg_flag);
         if (err == cudaSuccess) err = e2;
     }
     delete e;
@@ -659,10 +787,21 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     int grid = (a.n_envs + W - 1) / W;
     const bool snap = (c->cfg.flags & LOB_FLAG_SNAPSHOT_CANCELS) != 0;
     const int variant = (d_l1 != nullptr ? 1 : 0) | (snap ? 2 : 0);
-    const int resident = c->num_sms * e->per_sm_v[variant];
+    int resident = c->num_sms * e->per_sm_v[variant];
     if (grid > resident) grid = resident;
+    a.n_seg = env_segments(a.n_envs, n_run, grid * W);
+    if (a.n_seg > 1) {  // the segmented instantiation's own occupancy
+        resident = c->num_sms * e->per_sm_v[variant | 4];
+        grid = (a.n_envs + W - 1) / W;
+        if (grid > resident) grid = resident;
+        a.n_seg = env_segments(a.n_envs, n_run, grid * W);
+    }
+    e->last_segments = a.n_seg;
+    a.pad2_ = 0;
+    a.seg_flag = e->d_seg_flag;
     void* args[] = {&a};
-    cudaError_t err = cudaLaunchKernel(env_kernel(c->K, d_l1 != nullptr, snap), dim3(grid),
+    cudaError_t err = cudaLaunchKernel(env_kernel(c->K, d_l1 != nullptr, snap, a.n_seg > 1),
+                                       dim3(grid),
                                        dim3(32 * W), args,
                                        (size_t)e->smem_per_cta, (cudaStream_t)stream);
     if (err != cudaSuccess) return lob_cuda_fail(err, "lob_env_run launch");
@@ -670,6 +809,8 @@ int lob_env_run(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env, int32
     e->launches += 1;
     return LOB_OK;
 }
+
+int32_t lob_env_segments(const lob_env* e) { return e ? e->last_segments : -1; }
 
 int lob_env_observe(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env,
                     const int32_t* d_l1, float* d_obs, void* stream)

@@ -178,3 +178,76 @@ def test_env_level1_trace_matches_oracle(eng, cap):
         r_, lv, f_, tr = oenv.step(stp, np.arange(0, n_env * per + 1, per), draws[t], t, l1=True)
         assert np.array_equal(g[t].reshape(-1, 4), tr), t
         assert out["reward"][t].cpu().numpy().tobytes() == r_.tobytes()
+
+
+@pytest.mark.parametrize("cap,n_env", [(100, 3000), (250, 3000)])
+def test_segmented_persistent_episode_equals_per_step(eng, cap, n_env):
+    """More environments than resident warps: the persistent launch hands out
+    segments of each episode (each resuming from what the previous one wrote
+    back).  Its results equal one launch per step and the oracle, also when
+    the same launch runs again and when it is replayed from a CUDA graph
+    (whose arguments never change: the segment flags carry a device epoch)."""
+    n_steps, per, tcap = 48, 20, 256
+    m, _ = episode_streams(n_env, n_steps, per, 515 + cap)
+    draws = lobgen.agent_draws(77, n_env, n_steps)
+    d = eng.messages_to_device(m)
+    dr = torch.from_numpy(draws.view(np.int32)).cuda()
+
+    def make():
+        e = eng.Engine(n_env, cap, tcap)
+        env = eng.Env(e, n_steps=n_steps, parent_qty=2000, agent_tid=AGENT, msgs_per_step=per)
+        return e, env, env.outputs(n_steps)
+
+    def snap(e, env, out):
+        torch.cuda.synchronize()
+        st, p0 = env.state()
+        o = {k: v.cpu().numpy().copy() for k, v in out.items()}
+        o["state"], o["p_init"] = st.cpu().numpy(), p0.cpu().numpy()
+        o.update({"book_" + k: v.cpu().numpy() for k, v in e.book().items()})
+        o["counters"] = e.stats()[0].cpu().numpy()
+        return o
+
+    # reference: one launch per step
+    e1, env1, out1 = make()
+    for t in range(n_steps):
+        env1.run(d, n_steps * per, t, 1, dr[t:t + 1], out1, row0=t)
+    ref = snap(e1, env1, out1)
+    assert env1.segments() == 1
+    # one persistent launch, twice on the same objects
+    e2, env2, out2 = make()
+    for rep in range(2):
+        e2.reset()
+        env2.reset()
+        env2.run(d, n_steps * per, 0, n_steps, dr, out2)
+        assert env2.segments() > 1, "the launch should split the episodes"
+        got = snap(e2, env2, out2)
+        for k, v in ref.items():
+            assert v.tobytes() == got[k].tobytes(), (rep, k)
+    # the persistent launch captured in a CUDA graph and replayed twice
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            e2.reset()
+            env2.reset()
+            env2.run(d, n_steps * per, 0, n_steps, dr, out2)
+    torch.cuda.current_stream().wait_stream(s)
+    for rep in range(2):
+        g.replay()
+        got = snap(e2, env2, out2)
+        for k, v in ref.items():
+            assert v.tobytes() == got[k].tobytes(), ("graph", rep, k)
+    assert int(e2.stats()[1].item()) == 0
+    # and the oracle on a few environments
+    sample = np.array([0, 1, n_env // 2, n_env - 1])
+    oenv, oouts = run_oracle(m.reshape(n_env, -1)[sample].reshape(-1), len(sample), n_steps, per,
+                             draws[:, sample], cap, tcap, 0.0)
+    for t in range(n_steps):
+        reward, lv, fills = oouts[t]
+        assert ref["reward"][t][sample].tobytes() == reward.tobytes(), t
+        assert np.array_equal(ref["fills"][t][sample], fills), t
+        assert np.array_equal(ref["bid_px"][t][sample], lv[0]), t
+    ob = oenv.books.book()
+    for k, v in ob.items():
+        assert np.array_equal(ref["book_" + k][sample], v), k
