@@ -62,6 +62,9 @@ def parse():
                     help="seconds of Poisson arrivals in the serving workload")
     ap.add_argument("--serving-budget-mib", type=int, default=32,
                     help="HBM budget of the serving leg in which admission binds")
+    ap.add_argument("--rl-forms", default="all",
+                    help="RL workload legs to run: all, or a comma list of per_step, "
+                         "persistent, graph, policy (a profiler can then select one)")
     return ap.parse_args()
 
 
@@ -692,9 +695,13 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
         return [v.clone() for v in out.values()] + [st, p0] + list(e.book().values())
 
     res = {"n_envs": n, "steps": steps, "msgs_per_step": per, "seed": w["seed"]}
+    want = set(args.rl_forms.split(",")) if args.rl_forms != "all" else {
+        "per_step", "persistent", "graph", "policy"}
     ref = None
     forms = {}
     for name, fn in (("per_step_launches", per_step), ("persistent_episode", persistent)):
+        if name.split("_")[0] not in want:
+            continue
         times = []
         for i in range(max(1, args.warmup) + max(2, args.steps // 3)):
             a, b = _events()
@@ -710,6 +717,18 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
             ref = snap
         else:
             res["persistent_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snap))
+    if "persistent" in want:
+        res["segments_per_episode"] = env.segments()
+    if want != {"per_step", "persistent", "graph", "policy"}:
+        # a subset of the legs (profiling): timings only
+        for name, ms in forms.items():
+            res[name] = {"ms_per_episode": round(ms, 3),
+                         "env_steps_per_s": round(n * steps / ms * 1e3, 1)}
+        env.close()
+        e.close()
+        del dm, out
+        torch.cuda.empty_cache()
+        return res
     # CUDA graph of the per-step form
     s2 = torch.cuda.Stream()
     s2.wait_stream(torch.cuda.current_stream())
@@ -1057,7 +1076,8 @@ def run_single(args):
     wl = args.workload
     if wl.startswith("rl_exec"):
         r = run_rl(args, rank, wl)
-        value, unit = r["persistent_episode"]["env_steps_per_s"], "env-steps/s"
+        leg = r.get("persistent_episode") or r.get("per_step_launches") or {}
+        value, unit = leg.get("env_steps_per_s"), "env-steps/s"
     elif wl.startswith("uneven"):
         r = run_uneven(args, rank)
         value, unit = r["natural"]["msgs_per_s"], UNIT
