@@ -865,6 +865,9 @@ def run_serving(args, rank):
                   "p50_window_gen_ms", "admission_wait_p50", "admission_wait_p99"):
             if rep.get(k) is not None:
                 rep[k] = round(rep[k], 4)
+        for v in rep.get("per_capacity", {}).values():
+            for k in ("p50_step_ms", "p99_step_ms"):
+                v[k] = round(v[k], 4)
         res[leg] = rep
         del srv
         torch.cuda.empty_cache()

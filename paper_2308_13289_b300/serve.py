@@ -364,8 +364,14 @@ class Server:
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         gen_ms = []
-        for p in self.pools.values():
+        per_pool = {}
+        for c, p in self.pools.items():
             p.flush()
+            if p.lat:
+                pl = np.repeat(np.asarray([ms for ms, _ in p.lat]), [n for _, n in p.lat])
+                per_pool[c] = {"p50_step_ms": float(np.percentile(pl, 50)),
+                               "p99_step_ms": float(np.percentile(pl, 99)),
+                               "episode_steps": int(len(pl))}
             for ms, n in p.lat:
                 lat.append(ms / 1e3)
                 weights.append(n)
@@ -390,6 +396,7 @@ class Server:
                 "hbm_budget_bytes": self.budget,
                 "hbm_reserved_bytes": sum(p.reserved_bytes for p in self.pools.values()),
                 "slots": {c: p.slots for c, p in self.pools.items()},
+                "per_capacity": per_pool,
                 "queue": queue_len}
 
     def _record(self, episodes, launched):
