@@ -35,8 +35,8 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert "sample" in cb
-    # the same sample as the engine arm's cpu_baseline (256 books by default)
-    assert cb["sample"].startswith("first 256 of 1024 books")
+    # the same sample as the engine arm's cpu_baseline (every book by default)
+    assert cb["sample"].startswith("first 1024 of 1024 books")
     assert cb["single_thread"]["value"] > 0 and "1 thread" in cb["single_thread"]["sample"]
     assert d["config"]["workload"] == "replay_1024x10k" and d["config"]["capacity"] == 100
 
