@@ -856,10 +856,23 @@ def run_serving(args, rank):
                                        / args.serving_window, 1),
            "offered_episode_steps_per_s": round(sum(e.n_steps for e in eps)
                                                 / args.serving_window, 1)}
+    # a sample checked against the oracle at full size: the shortest episode
+    # of each capacity and the longest one (whole episodes are replayed on one
+    # host thread)
+    size = lambda e: e.n_steps * e.msgs_per_step  # noqa: E731
+    sample = []
+    for c in w["capacities"]:
+        mine = [e for e in eps if e.capacity == c]
+        if mine:
+            sample.append(min(mine, key=size))
+    if eps:
+        sample.append(max(eps, key=size))
     for leg, budget in (("uncontended", 2 << 30), ("contended", args.serving_budget_mib << 20)):
         srv = Server(capacities=w["capacities"], seed=w["seed"], hbm_budget=budget,
-                     msgs_per_step=w["msgs_per_step"])
+                     msgs_per_step=w["msgs_per_step"], capture_ids=[e.id for e in sample])
         rep = srv.run([copy.copy(e) for e in eps], clock="wall")
+        if rank == 0:
+            rep["parity"] = serving_parity(srv, sample, w["seed"])
         q = rep.pop("queue")
         rep["queue_samples"] = [(round(t, 3), n) for t, n in q[::max(1, len(q) // 20)]]
         for k in ("wall_s", "steps_per_s", "msgs_per_s", "p50_step_ms", "p99_step_ms",
@@ -873,6 +886,30 @@ def run_serving(args, rank):
         del srv
         torch.cuda.empty_cache()
     return res
+
+
+def serving_parity(srv, sample, seed, tcap=2048):
+    """Final book and counters of each sampled episode against the oracle
+    replaying the episode's stream (stream id = episode id) step by step."""
+    import lobgen
+    import oracle
+    params = lobgen.make_params(seed, "pm1")
+    ok, msgs = True, 0
+    for ep in sample:
+        hs = lobgen.HostStreams(params, 1, stream_ids=[ep.id])
+        o = oracle.Oracle(1, ep.capacity, tcap)
+        for _ in range(ep.n_steps):
+            m, off = hs.advance([ep.msgs_per_step], threads=1)
+            o.process(m, off, threads=1)
+            msgs += len(m)
+        got = srv.final_books.get(ep.id)
+        if got is None:
+            ok = False
+            continue
+        ok &= all(np.array_equal(v[0], got[k]) for k, v in o.book().items())
+        ok &= np.array_equal(o.counters()[0], srv.final_counters[ep.id])
+    return {"episodes_checked": len(sample), "messages": msgs, "bit_exact": bool(ok),
+            "capacities": [e.capacity for e in sample]}
 
 
 def eng_book_bytes(cap):

@@ -30,7 +30,8 @@ events on the processing stream; the generator's time per tick is reported
 beside it.  With collect=True (tests) every tick is synchronous, timed on the
 host, and the per-step levels and trade counts of every episode are kept.
 keep_final=True keeps every episode's final book and counters, captured on the
-device in stream order when it finishes (valid in both modes).
+device in stream order when it finishes (valid in both modes); capture_ids
+keeps them for the listed episode ids only (a sample to check at full size).
 """
 from __future__ import annotations
 
@@ -262,13 +263,14 @@ class Server:
 
     def __init__(self, capacities=(100, 250, 500), hbm_budget=2 << 30, trade_capacity=2048,
                  depth=10, seed=20230829, max_slots=4096, collect=False, keep_final=False,
-                 msgs_per_step=(100, 500)):
+                 msgs_per_step=(100, 500), capture_ids=None):
         self.params = lobgen.make_params(seed, "pm1")
         self.depth = depth
         self.budget = hbm_budget
         self.tcap = trade_capacity
         self.collect = collect
         self.keep_final = keep_final or collect
+        self.capture_ids = set(capture_ids) if capture_ids else set()
         lo, hi = msgs_per_step
         self.pools = {}
         for c in capacities:
@@ -347,9 +349,11 @@ class Server:
             for p, act, _ in launched:
                 p.step[act] += 1
                 ended = act[p.step[act] >= p.n_steps[act]]
-                if len(ended) and self.keep_final:
+                keep = [s for s in ended if self.keep_final or
+                        episodes[int(p.ep[s])].id in self.capture_ids]
+                if keep:
                     cap = p.capture_final()
-                    for s in ended:
+                    for s in keep:
                         finals.append((episodes[int(p.ep[s])].id, int(s), cap))
                 for s in ended:
                     ep = episodes[int(p.ep[s])]
