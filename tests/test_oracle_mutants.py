@@ -52,6 +52,22 @@ REWARD_MUTANTS = {
 }
 
 
+# mistakes in snapshot initialisation and the snapshot cancel rule (Sec. 5.1.1)
+SNAPSHOT_MUTANTS = {
+    "snapshot_cancel_strict": ("if (q.oid <= SNAPSHOT_OID_MAX) {", "if (q.oid < SNAPSHOT_OID_MAX) {"),
+    "snapshot_cancel_takes_latest": ("""                if (q.oid <= SNAPSHOT_OID_MAX) {
+                    o = &q;
+                    break;
+                }""", """                if (q.oid <= SNAPSHOT_OID_MAX) {
+                    o = &q;
+                }"""),
+    "snapshot_cancel_any_order": ("if (q.oid <= SNAPSHOT_OID_MAX) {", "if (true) {"),
+    "init_first_oid": ("int32_t next_oid = -9000;", "int32_t next_oid = -9001;"),
+    "init_oids_count_up": ("next_oid--, 0, time_ns", "next_oid++, 0, time_ns"),
+    "init_ignores_zero_volume": ("px[listed] > 0 && qty[listed] > 0", "px[listed] > 0"),
+}
+
+
 def _build_mutant(tmp_path, name, old, new):
     src = open(SRC).read()
     assert src.count(old) == 1, name
@@ -152,3 +168,79 @@ def test_unmutated_copy_passes_env_episodes(tmp_path):
                                     "int oracle_abi_version(void) { return 1; }",
                                     "int oracle_abi_version(void) { return 1; }"))
     assert _env_golden_ok(lib)
+
+
+def _snapshot_golden_ok(lib):
+    """The hand-worked snapshot cases of tests/test_snapshot_init.py, run
+    through a compiled oracle: initialisation of three books, and the
+    price-matched cancels (one snapshot order per level, and two at one
+    price)."""
+    import test_snapshot_init as ts
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.oracle_create.restype = vp
+    lib.oracle_create.argtypes = [i32] * 5
+    lib.oracle_destroy.argtypes = [vp]
+    lib.oracle_init_from_levels.restype = i32
+    lib.oracle_init_from_levels.argtypes = [vp] * 5 + [i32, ctypes.c_int64]
+    lib.oracle_process.restype = ctypes.c_int64
+    lib.oracle_process.argtypes = [vp, vp, vp, vp, i32, i32]
+    lib.oracle_get_book.argtypes = [vp] * 7
+
+    def book(h, n, cap):
+        shp = (n, 2, cap)
+        out = {k: np.empty(shp, np.int32) for k in ("price", "qty", "oid", "tid")}
+        out["time_ns"] = np.empty(shp, np.int64)
+        out["count"] = np.empty((n, 2), np.int32)
+        lib.oracle_get_book(h, *[vp(out[k].ctypes.data) for k in
+                                 ("price", "qty", "oid", "tid", "time_ns", "count")])
+        return out
+
+    def init(h, levels, t=0):
+        a = [np.ascontiguousarray(x, np.int32) for x in levels]
+        return lib.oracle_init_from_levels(h, *[vp(x.ctypes.data) for x in a], a[0].shape[1], t)
+
+    def run(h, rows):
+        m = ts._msg(rows)
+        off = np.array([0, len(m)], np.int64)
+        lib.oracle_process(h, vp(m.ctypes.data), vp(off.ctypes.data), None, 1, 1)
+
+    ok = True
+    h = lib.oracle_create(3, 4, 8, 0, 0)
+    ok &= init(h, ts._levels_case(), 77) == 1
+    bk = book(h, 3, 4)
+    ok &= all(bk[k].tolist() == v for k, v in ts.HAND_INIT.items())
+    lib.oracle_destroy(h)
+    # one snapshot order per level (the cancel-rule example)
+    h = lib.oracle_create(1, 8, 16, 0, 2)
+    init(h, (np.array([[100, 99]]), np.array([[5, 7]]), np.array([[101, 103]]),
+             np.array([[4, 6]])))
+    run(h, [(2, ts.BID, 99, 3, 555), (3, ts.ASK, 103, 6, 777), (2, ts.BID, 98, 1, 888),
+            (2, ts.BID, 101, 1, 889), (1, ts.BID, 99, 2, 10), (2, ts.BID, 99, 4, 556),
+            (2, ts.BID, 99, 1, 557), (2, ts.BID, 99, 1, 10), (2, ts.BID, 100, 1, 558)])
+    bk = book(h, 1, 8)
+    ok &= bk["oid"][0, 0, :2].tolist() == [-9000, 10] and bk["qty"][0, 0, :2].tolist() == [4, 1]
+    ok &= bk["count"][0].tolist() == [2, 1]
+    lib.oracle_destroy(h)
+    # two snapshot orders at one price
+    h = lib.oracle_create(1, 8, 16, 0, 2)
+    init(h, (np.array([[100, 100, 99]]), np.array([[5, 3, 7]]), np.array([[101, 102, 103]]),
+             np.array([[4, 4, 4]])))
+    run(h, [(2, ts.BID, 100, 2, 555), (3, ts.BID, 100, 3, 556), (2, ts.BID, 100, 1, 557)])
+    bk = book(h, 1, 8)
+    ok &= bk["oid"][0, 0, :2].tolist() == [-9001, -9002] and bk["qty"][0, 0, :2].tolist() == [2, 7]
+    lib.oracle_destroy(h)
+    return bool(ok)
+
+
+@pytest.mark.parametrize("name", sorted(SNAPSHOT_MUTANTS))
+def test_snapshot_examples_reject_mutant(tmp_path, name):
+    old, new = SNAPSHOT_MUTANTS[name]
+    lib = ctypes.CDLL(_build_mutant(tmp_path, name, old, new))
+    assert not _snapshot_golden_ok(lib), "planted snapshot mistake %r went unnoticed" % name
+
+
+def test_unmutated_copy_passes_snapshot_examples(tmp_path):
+    lib = ctypes.CDLL(_build_mutant(tmp_path, "identity_snap",
+                                    "int oracle_abi_version(void) { return 1; }",
+                                    "int oracle_abi_version(void) { return 1; }"))
+    assert _snapshot_golden_ok(lib)

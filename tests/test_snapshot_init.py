@@ -168,6 +168,29 @@ def test_oracle_init_from_levels_then_cancel_by_price():
         assert np.array_equal(v, ref[k]), k
 
 
+def test_oracle_snapshot_cancel_takes_the_earliest_of_equal_price_orders():
+    """Two listed levels at one price become two snapshot orders of one level,
+    in listed order; a cancel of an unknown id at that price reduces the
+    earlier one (its priority is higher), and after it leaves, the later."""
+    cap = 8
+    o = oracle.Oracle(1, cap, 16, snapshot_cancels=True)
+    bp = np.array([[100, 100, 99]], np.int32)
+    bq = np.array([[5, 3, 7]], np.int32)
+    ap = np.array([[101, 102, 103]], np.int32)
+    aq = np.array([[4, 4, 4]], np.int32)
+    o.init_from_levels(bp, bq, ap, aq)
+    msgs = _msg([
+        (2, BID, 100, 2, 555),   # unknown id at 100: the earlier order -9000, 5 -> 3
+        (3, BID, 100, 3, 556),   # delete unknown id at 100: -9000 (3 left) leaves
+        (2, BID, 100, 1, 557),   # now the later one, -9001: 3 -> 2
+    ])
+    o.process(msgs, np.array([0, len(msgs)], np.int64))
+    bk = o.book()
+    assert bk["oid"][0, 0, :2].tolist() == [-9001, -9002]
+    assert bk["qty"][0, 0, :2].tolist() == [2, 7]
+    assert _levels(o)[0] == [(100, 2), (99, 7)]
+
+
 def _snapshot_workload(n_books, depth, n_msgs, seed):
     """Seeded level snapshots (10 levels a side, one tick apart around a mid
     price) and per-book streams: lobgen flow with, interleaved, cancels and
@@ -317,3 +340,52 @@ def test_gpu_init_from_levels_rejects_bad_depth():
     with pytest.raises(eng.LobError):
         e.init_from_levels(z, z, z, z)  # depth 9 > capacity 8
     e.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("cap", [32, 100, 300])
+def test_gpu_snapshot_cancels_at_equal_price_levels(cap):
+    """Snapshots listing several levels at one price (several snapshot orders
+    in one level): price-matched cancels take them earliest first, on the GPU
+    as in the oracle, in both book layouts."""
+    import torch
+
+    import paper_2308_13289_b300 as eng
+    n_books, depth, tcap = 48, 12, 1024
+    rng = np.random.default_rng(cap)
+    mid = rng.integers(1_000, 9_000, n_books)
+    # each price listed up to three times in a row
+    step = (rng.random((n_books, depth)) < 0.4).astype(np.int64)
+    step[:, 0] = 0
+    bp = (mid[:, None] - 1 - np.cumsum(step, axis=1)).astype(np.int32)
+    ap = (mid[:, None] + 1 + np.cumsum(step, axis=1)).astype(np.int32)
+    bq = rng.integers(1, 50, (n_books, depth)).astype(np.int32)
+    aq = rng.integers(1, 50, (n_books, depth)).astype(np.int32)
+    rows, offs = [], [0]
+    for b in range(n_books):
+        k = 200
+        side = np.where(rng.random(k) < 0.5, BID, ASK)
+        lvl = rng.integers(0, depth, k)
+        m = np.zeros(k, dtype=lobgen.MSG_DTYPE)
+        m["type"] = np.where(rng.random(k) < 0.7, 2, 3)
+        m["side"] = side
+        m["price"] = np.where(side == BID, bp[b, lvl], ap[b, lvl])
+        m["qty"] = rng.integers(1, 30, k)
+        m["oid"] = 2_000_000_000 - np.arange(k)
+        m["tid"] = 5
+        m["time_ns"] = np.arange(k)
+        rows.append(m)
+        offs.append(offs[-1] + k)
+    msgs, off = np.concatenate(rows), np.array(offs, np.int64)
+    e = eng.Engine(n_books, cap, tcap, snapshot_cancels=True)
+    e.init_from_levels(*[torch.from_numpy(x).cuda() for x in (bp, bq, ap, aq)])
+    e.process_batch(eng.messages_to_device(msgs), torch.from_numpy(off).cuda())
+    g = gpu_outputs(e)
+    e.close()
+    o = oracle.Oracle(n_books, cap, tcap, snapshot_cancels=True)
+    assert o.init_from_levels(bp, bq, ap, aq) == 0
+    o.process(msgs, off)
+    ref = oracle_outputs(o)
+    assert_same(g, ref)
+    hit = oracle.COUNTERS.index("cancel_hit")
+    assert ref["counters"][:, hit].sum() > n_books * 100
