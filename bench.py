@@ -700,8 +700,9 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
         "per_step", "persistent", "graph", "policy"}
     ref = None
     forms = {}
-    for name, fn in (("per_step_launches", per_step), ("persistent_episode", persistent)):
-        if name.split("_")[0] not in want:
+    for name, form, fn in (("per_step_launches", "per_step", per_step),
+                           ("persistent_episode", "persistent", persistent)):
+        if form not in want:
             continue
         times = []
         for i in range(max(1, args.warmup) + max(2, args.steps // 3)):
