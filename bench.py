@@ -719,6 +719,10 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
             ref = snap
         else:
             res["persistent_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snap))
+    ran = {"per_step": "per_step_launches", "persistent": "persistent_episode"}
+    missing = [f for f, leg in ran.items() if f in want and leg not in forms]
+    if missing:
+        raise RuntimeError("RL legs requested but not run: %s" % missing)
     if "persistent" in want:
         res["segments_per_episode"] = env.segments()
     if want != {"per_step", "persistent", "graph", "policy"}:
