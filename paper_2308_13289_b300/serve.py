@@ -101,6 +101,23 @@ def _p(t, byte_off=0):
     return ctypes.c_void_p(t.data_ptr() + byte_off)
 
 
+_cudart = None
+
+
+def _memcpy_h2d_async():
+    """cudaMemcpyAsync of the CUDA runtime torch loaded (raw pointers and
+    stream handle: a tick's upload without torch's stream bookkeeping)."""
+    global _cudart
+    if _cudart is None:
+        lib = ctypes.CDLL("libcudart.so.%d" % int(torch.version.cuda.split(".")[0]))
+        fn = lib.cudaMemcpyAsync
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                       ctypes.c_void_p]
+        _cudart = fn
+    return _cudart
+
+
 class _Pool:
     """Resident slots of one capacity class: an engine context over all slots,
     per-slot generator state, double-buffered step windows, two streams."""
@@ -108,8 +125,10 @@ class _Pool:
     def __init__(self, capacity, slots, trade_capacity, depth, params, max_mps, collect):
         self.capacity, self.slots, self.depth, self.params = capacity, slots, depth, params
         self.max_mps = max_mps
-        self.stream = torch.cuda.Stream()   # processing
-        self.gstream = torch.cuda.Stream()  # window generation
+        # processing ahead of window generation when both have blocks waiting
+        # for an SM (the step latency is the processing's)
+        self.stream = torch.cuda.Stream(priority=-1)  # processing
+        self.gstream = torch.cuda.Stream(priority=0)  # window generation
         S = slots
         # packed per-tick upload (int64 words): offsets [S+1] | counts [S] |
         # restart stream ids [S] | active slot ids (int32) [S] | restart slots (int32) [S]
@@ -134,12 +153,26 @@ class _Pool:
         self.reserved_bytes = (S * (book_bytes(capacity) + 8 + 32 * trade_capacity + 8
                                     + 8 * N_COUNTERS + GEN_STATE_BYTES)
                                + 2 * S * max_mps * MSG_BYTES)
+        # device addresses and handles used every tick (the buffers never move)
+        self.h_ps = ctypes.c_void_p(self.stream.cuda_stream)
+        self.h_gs = ctypes.c_void_p(self.gstream.cuda_stream)
+        self.a_win = [_p(w) for w in self.win]
+        self.a_pack = [dict(off=_p(d), cnt=_p(d, 8 * self.o_cnt), sid=_p(d, 8 * self.o_sid),
+                            ids=_p(d, 8 * self.o_ids), rid=_p(d, 8 * self.o_rid))
+                       for d in self.d_pack]
+        self.a_states, self.a_pools = _p(self.g_states), _p(self.g_pools)
+        self.a_geo_px, self.a_geo_q = _p(self.geo_px), _p(self.geo_q)
+        self.a_levels = [_p(x) for x in self.levels]
+        self.a_tcount = _p(self.d_tcount)
+        self.params_ref = ctypes.byref(self.params)
+        self.memcpy = _memcpy_h2d_async()
         self.ev_gen = [torch.cuda.Event() for _ in range(2)]   # windows k ready
         self.ev_used = [torch.cuda.Event() for _ in range(2)]  # windows k consumed
         self.ring = []
         for _ in range(RING):
             pack = torch.empty(self.pack_words, dtype=torch.int64).pin_memory()
-            self.ring.append(dict(pack=pack, np=pack.numpy(), copied=torch.cuda.Event(),
+            self.ring.append(dict(pack=pack, np=pack.numpy(), a_pack=_p(pack),
+                                  copied=torch.cuda.Event(),
                                   g0=torch.cuda.Event(enable_timing=True),
                                   g1=torch.cuda.Event(enable_timing=True),
                                   t0=torch.cuda.Event(enable_timing=True),
@@ -205,47 +238,45 @@ class _Pool:
         buf[self.o_ids:].view(np.int32)[:n] = act
         self.restart = []
         k = self.tick & 1
-        dp = self.d_pack[k]
+        ap = self.a_pack[k]
         lg = lobgen.cuda_lib()
+        lb = lib()
         gs, ps = self.gstream, self.stream
-        g_s = ctypes.c_void_p(gs.cuda_stream)
-        p_s = ctypes.c_void_p(ps.cuda_stream)
         # generator stream: the windows of this tick (buffer k is free once
         # the processing of tick-2 has consumed it)
         gs.wait_event(self.ev_used[k])
-        with torch.cuda.stream(gs):
-            dp.copy_(st["pack"], non_blocking=True)
-            st["copied"].record(gs)
-            st["busy"], st["timed"], st["n"] = True, timing, n
-            if timing:
-                st["g0"].record(gs)
-            if nr and lg.lobgen_dev_init_ids(ctypes.byref(self.params), nr, _p(dp, 8 * self.o_rid),
-                                             _p(dp, 8 * self.o_sid), _p(self.g_states), g_s) != 0:
-                raise RuntimeError("lobgen_dev_init_ids failed")
-            if lg.lobgen_dev_advance(ctypes.byref(self.params), _p(self.geo_px), _p(self.geo_q), n,
-                                     _p(dp, 8 * self.o_ids), _p(self.g_states), _p(self.g_pools),
-                                     _p(dp, 8 * self.o_cnt), _p(dp), _p(self.win[k]), g_s) != 0:
-                raise RuntimeError("lobgen_dev_advance failed")
-            if timing:
-                st["g1"].record(gs)
-            self.ev_gen[k].record(gs)
+        if self.memcpy(ap["off"], st["a_pack"], 8 * self.pack_words, 1, self.h_gs) != 0:
+            raise RuntimeError("cudaMemcpyAsync of the tick's upload failed")
+        st["copied"].record(gs)
+        st["busy"], st["timed"], st["n"] = True, timing, n
+        if timing:
+            st["g0"].record(gs)
+        if nr and lg.lobgen_dev_init_ids(self.params_ref, nr, ap["rid"], ap["sid"], self.a_states,
+                                         self.h_gs) != 0:
+            raise RuntimeError("lobgen_dev_init_ids failed")
+        if lg.lobgen_dev_advance(self.params_ref, self.a_geo_px, self.a_geo_q, n, ap["ids"],
+                                 self.a_states, self.a_pools, ap["cnt"], ap["off"], self.a_win[k],
+                                 self.h_gs) != 0:
+            raise RuntimeError("lobgen_dev_advance failed")
+        if timing:
+            st["g1"].record(gs)
+        self.ev_gen[k].record(gs)
         # processing stream
         ps.wait_event(self.ev_gen[k])
-        with torch.cuda.stream(ps):
-            if timing:
-                st["t0"].record(ps)
-            h = self.engine.h
-            if nr and lib().lob_reset_books(h, _p(dp, 8 * self.o_rid), nr, p_s) != 0:
-                raise RuntimeError("lob_reset_books failed")
-            if lib().lob_process_batch(h, _p(self.win[k]), _p(dp), _p(dp, 8 * self.o_ids), n,
-                                       p_s) != 0:
-                raise RuntimeError("lob_process_batch failed")
-            lob_get_levels(h, self.depth, *self.levels, stream=ps)
-            if self.collect:
-                lib().lob_get_trades(h, None, _p(self.d_tcount), p_s)
-            if timing:
-                st["t1"].record(ps)
-            self.ev_used[k].record(ps)
+        if timing:
+            st["t0"].record(ps)
+        h = self.engine.h
+        if nr and lb.lob_reset_books(h, ap["rid"], nr, self.h_ps) != 0:
+            raise RuntimeError("lob_reset_books failed")
+        if lb.lob_process_batch(h, self.a_win[k], ap["off"], ap["ids"], n, self.h_ps) != 0:
+            raise RuntimeError("lob_process_batch failed")
+        if lb.lob_get_levels(h, self.depth, *self.a_levels, self.h_ps) != 0:
+            raise RuntimeError("lob_get_levels failed")
+        if self.collect:
+            lb.lob_get_trades(h, None, self.a_tcount, self.h_ps)
+        if timing:
+            st["t1"].record(ps)
+        self.ev_used[k].record(ps)
         self.tick += 1
         return act, int(cnt.sum())
 
@@ -285,18 +316,35 @@ class Server:
     def footprint(self, ep):
         return footprint_bytes(ep.capacity, self.tcap, ep.msgs_per_step)
 
-    def _can_admit(self, ep):
-        pool = self.pools.get(ep.capacity)
-        if pool is None:
-            raise ValueError("no pool for capacity %d" % ep.capacity)
-        return bool(pool.free) and self.used + self.footprint(ep) <= self.budget
+    def _admit_waiting(self, episodes, waiting, fps, min_fp, now):
+        """First fit in arrival order; stops as soon as no waiting episode
+        could fit the budget left, and passes over classes without a free
+        slot.  Returns the episodes still waiting."""
+        still = collections.deque()
+        while waiting:
+            if self.used + min_fp > self.budget:
+                still.extend(waiting)
+                break
+            i = waiting.popleft()
+            ep = episodes[i]
+            pool = self.pools.get(ep.capacity)
+            if pool is None:
+                raise ValueError("no pool for capacity %d" % ep.capacity)
+            if pool.free and self.used + fps[i] <= self.budget:
+                pool.admit(i, ep)
+                self.used += fps[i]
+                ep.admitted = now
+            else:
+                still.append(i)
+        return still
 
     def run(self, episodes, clock="wall", max_ticks=None):
         """Serve `episodes` (arrival in seconds for clock='wall', in ticks for
         clock='virtual'); returns a report dict."""
-        for ep in episodes:
-            if self.footprint(ep) > self.budget:
-                raise ValueError("episode %d alone exceeds the HBM budget" % ep.id)
+        fps = [self.footprint(ep) for ep in episodes]
+        if any(f > self.budget for f in fps):
+            raise ValueError("an episode alone exceeds the HBM budget")
+        min_fp = min(fps) if fps else 0
         order = sorted(range(len(episodes)), key=lambda i: episodes[i].arrival)
         pending = collections.deque(order)
         waiting = collections.deque()
@@ -310,17 +358,7 @@ class Server:
             now = (time.perf_counter() - t0) if clock == "wall" else float(tick)
             while pending and episodes[pending[0]].arrival <= now:
                 waiting.append(pending.popleft())
-            # first fit, in arrival order
-            still = collections.deque()
-            for i in waiting:
-                ep = episodes[i]
-                if self._can_admit(ep):
-                    self.pools[ep.capacity].admit(i, ep)
-                    self.used += self.footprint(ep)
-                    ep.admitted = now
-                else:
-                    still.append(i)
-            waiting = still
+            waiting = self._admit_waiting(episodes, waiting, fps, min_fp, now)
             queue_len.append((now, len(waiting)))
             active = sum(p.n_active for p in self.pools.values())
             max_active = max(max_active, active)
@@ -356,12 +394,12 @@ class Server:
                     for s in keep:
                         finals.append((episodes[int(p.ep[s])].id, int(s), cap))
                 for s in ended:
-                    ep = episodes[int(p.ep[s])]
-                    ep.done = now_after
+                    i = int(p.ep[s])
+                    episodes[i].done = now_after
                     p.ep[s] = -1
                     p.n_active -= 1
                     p.free.append(int(s))
-                    self.used -= self.footprint(ep)
+                    self.used -= fps[i]
             tick += 1
             if max_ticks is not None and tick >= max_ticks:
                 break
