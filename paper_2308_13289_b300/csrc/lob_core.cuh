@@ -209,21 +209,23 @@ __device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b)
 
 // ---------------------------------------------------------------- primitives
 
-// Shift the slots from p on right by one and place `val` at slot p, with the
-// left neighbour's last slot already fetched (prev = __shfl_up_sync(kFull,
-// v[K - 1], 1)), so that the shuffle can be issued before p is known.  Slots
-// at or past the new count hold no order and every reader bounds its slots by
-// the count, so they take whatever the shift brings (no upper bound to test).
+// Insert `val` into a lane's slots, the place given per slot: in[j + 1] says
+// whether slot l*K+j keeps its order (it ranks before the new one), in[0] the
+// same of the slot to its left (slot -1 keeps).  A slot that does not keep
+// takes `val` when its left neighbour keeps and the neighbour's order when it
+// does not; `prev` is the left neighbour's last slot, fetched beforehand
+// (__shfl_up_sync(kFull, v[K - 1], 1)) so that the shuffle can be issued
+// before the place is known.  Slots at or past the new count hold no order and
+// every reader bounds its slots by the count, so they take whatever the shift
+// brings.
 template <int K, typename T>
-__device__ __forceinline__ void shift_in_prev(T (&v)[K], int p, T val, T prev)
+__device__ __forceinline__ void shift_in_pred(T (&v)[K], const bool (&in)[K + 1], T val, T prev)
 {
-    const int l = lane_id();
     T nv[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-        const int s = l * K + j;
         T left = (j == 0) ? prev : v[j - 1];
-        nv[j] = (s == p) ? val : ((s > p) ? left : v[j]);
+        nv[j] = in[j + 1] ? v[j] : (in[j] ? val : left);
     }
 #pragma unroll
     for (int j = 0; j < K; ++j) v[j] = nv[j];
@@ -231,7 +233,7 @@ __device__ __forceinline__ void shift_in_prev(T (&v)[K], int p, T val, T prev)
 
 // shift_out with the right neighbour's first slot already fetched
 // (next = __shfl_down_sync(kFull, v[0], 1)); slots past the new count take
-// whatever the shift brings, as in shift_in_prev.
+// whatever the shift brings, as in shift_in_pred.
 template <int K, typename T>
 __device__ __forceinline__ void shift_out_next(T (&v)[K], int p, T next)
 {
@@ -539,6 +541,7 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
         g_add_order<K, X>(bk.template side<X>(), n, cap, rule, P, Q, oid, tid, tlo, thi, ctr);
         return;
     }
+    static_assert(Book::kInRegisters || Book::kGrouped, "add_order: register or grouped books");
     const int l = lane_id();
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<X>(tmp);
@@ -550,32 +553,39 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
     const int32_t pv_tid = __shfl_up_sync(kFull, v.tid[K - 1], 1);
     const int32_t pv_tlo = __shfl_up_sync(kFull, v.tlo[K - 1], 1);
     const int32_t pv_thi = __shfl_up_sync(kFull, v.thi[K - 1], 1);
-    // insertion point: number of resting orders with a price at least as good
-    int p = 0;
-#pragma unroll
-    for (int j = 0; j < K; ++j)
-        p += __popc(__ballot_sync(kFull, l * K + j < n && at_least<X>(v.px[j], P)));
     const bool full = n >= cap;
-    if (full && (rule != 0 || p >= cap)) {
-        ctr.rejected += 1;
-        ctr.rejected_qty += Q;
-        return;
-    }
-    // full side: the worst order (slot cap-1) has a strictly worse price and
-    // is evicted
     if (full) {
+        // the worst order (slot cap-1) is evicted if its price is strictly
+        // worse than P, else the new order is rejected
+        const int32_t worst = slot_value<K>(v.px, cap - 1);
+        if (rule != 0 || at_least<X>(worst, P)) {
+            ctr.rejected += 1;
+            ctr.rejected_qty += Q;
+            return;
+        }
         ctr.evicted += 1;
         ctr.evicted_qty += slot_value<K>(v.q, cap - 1);
     }
+    // The side is in priority order, so the resting orders priced at least as
+    // well as P are a prefix of the slots, and the new order goes where that
+    // prefix ends.  Each slot decides from its own price and its left
+    // neighbour's: it keeps its order inside the prefix, takes the new order
+    // right after it, and takes its left neighbour's order further on (slots
+    // past the new count take whatever the shift brings).  Slot -1 counts as
+    // inside the prefix.
+    bool in[K + 1];
+    in[0] = l == 0 || (l * K - 1 < n && at_least<X>(pv_px, P));
+#pragma unroll
+    for (int j = 0; j < K; ++j) in[j + 1] = l * K + j < n && at_least<X>(v.px[j], P);
+    const bool top = n == 0 || !at_least<X>(bk.template best_px<X>(n), P);
     const int n_after = full ? cap : n + 1;
-    shift_in_prev<K>(v.px, p, P, pv_px);
-    shift_in_prev<K>(v.q, p, Q, pv_q);
-    shift_in_prev<K>(v.oid, p, oid, pv_oid);
-    shift_in_prev<K>(v.tid, p, tid, pv_tid);
-    shift_in_prev<K>(v.tlo, p, tlo, pv_tlo);
-    shift_in_prev<K>(v.thi, p, thi, pv_thi);
-    bk.template release<X>(v, lane_touches<K>(p, n_after));
-    if (p == 0) bk.template set_best<X>(P);
+    shift_in_pred<K>(v.px, in, P, pv_px);
+    shift_in_pred<K>(v.q, in, Q, pv_q);
+    shift_in_pred<K>(v.oid, in, oid, pv_oid);
+    shift_in_pred<K>(v.tid, in, tid, pv_tid);
+    shift_in_pred<K>(v.tlo, in, tlo, pv_tlo);
+    shift_in_pred<K>(v.thi, in, thi, pv_thi);
+    if (top) bk.template set_best<X>(P);
     n = n_after;
     ctr.rested += 1;
 }
@@ -607,7 +617,7 @@ __device__ __forceinline__ void cancel_order(Book& bk, int& n, int32_t oid, int3
     }
     if (hit == 0) return;  // not live on this side: no-op (counted at the end)
     ctr.cancel_hit += 1;
-    const int L = __ffs(hit) - 1;
+    const int L = __popc(~hit & (hit - 1u));  // lowest set bit: trailing zeros
     // each lane picks its own candidate, so both values leave lane L at once
     const int32_t q_mine = pick<K>(v.q, jj < 0 ? 0 : jj);
     const int j_hit = __shfl_sync(kFull, jj, L);
