@@ -926,43 +926,88 @@ __device__ __forceinline__ void g_add_order(char* side, int& n, int cap, int rul
 {
     const GSide<K> sd{side};
     const int l = lane_id();
-    // p = orders at least as good as P, the top p indices n-p .. n-1: lane l
-    // looks at priority ranks l and l+32 of a 64-order window from the top;
-    // the side is sorted, so the ranks that hold such an order are a prefix
-    int p = 0;
-#pragma unroll 1
-    for (int top = n; top > 0; top -= 64) {
-        const int i0 = top - 1 - l, i1 = top - 33 - l;
-        const bool ok0 = i0 >= 0 && at_least<X>(sd.px()[i0 >= 0 ? i0 : 0], P);
-        const bool ok1 = i1 >= 0 && at_least<X>(sd.px()[i1 >= 0 ? i1 : 0], P);
-        const int c = __popc(__ballot_sync(kFull, ok0)) + __popc(__ballot_sync(kFull, ok1));
-        p += c;
-        if (c < 64) break;
-    }
-    const bool full = n >= cap;
-    if (full && (rule != 0 || p >= cap)) {
-        ctr.rejected += 1;
-        ctr.rejected_qty += Q;
-        return;
-    }
-    if (full) {
-        // the worst order (index 0) has a strictly worse price and is evicted:
-        // every other order moves down one
+    if (n >= cap) {
+        // full side: the worst order (index 0) is evicted if its price is
+        // strictly worse than P (every other order moves down one), else the
+        // new order is rejected
+        const int32_t worst = sd.px()[0];
+        if (rule != 0 || at_least<X>(worst, P)) {
+            ctr.rejected += 1;
+            ctr.rejected_qty += Q;
+            return;
+        }
         ctr.evicted += 1;
         ctr.evicted_qty += sd.qty()[0];
         g_move_down<K>(sd, 1, n);
         n -= 1;
         __syncwarp();
     }
-    // the new order goes below the p orders at least as good, which move up
-    const int lo = n - p;
-    g_move_up<K>(sd, lo, n);
-    if (l == 0) {
-        sd.px()[lo] = P;
-        sd.qty()[lo] = Q;
-        sd.oid()[lo] = oid;
-        sd.tid()[lo] = tid;
-        sd.tm()[lo] = (int64_t)(((uint64_t)(uint32_t)thi << 32) | (uint32_t)tlo);
+    // The orders at least as good as P are the top p indices n-p .. n-1 (the
+    // side is sorted); they move up one and the new order takes index n-p.
+    // The 64 best orders (ranks l and l+32, indices n-1-l and n-33-l) are
+    // loaded whole; when rank 63 is not among them (p < 64), each of those
+    // orders moves from its own comparison, and the last of them (or lane 0
+    // for p = 0) places the new order: no count, no second load.
+    const int i0 = n - 1 - l, i1 = n - 33 - l;
+    const int k0 = i0 >= 0 ? i0 : 0, k1 = i1 >= 0 ? i1 : 0;
+    const int32_t p0 = sd.px()[k0], p1 = sd.px()[k1];
+    const int32_t q0 = sd.qty()[k0], o0 = sd.oid()[k0], t0 = sd.tid()[k0];
+    const int32_t q1 = sd.qty()[k1], o1 = sd.oid()[k1], t1 = sd.tid()[k1];
+    const int64_t e0 = sd.tm()[k0], e1 = sd.tm()[k1];
+    const bool ok0 = i0 >= 0 && at_least<X>(p0, P);
+    const bool ok1 = i1 >= 0 && at_least<X>(p1, P);
+    const unsigned b0 = __ballot_sync(kFull, ok0), b1 = __ballot_sync(kFull, ok1);
+    const int64_t tnew = (int64_t)(((uint64_t)(uint32_t)thi << 32) | (uint32_t)tlo);
+    if ((b1 >> 31) == 0u) {
+        // does the next rank (l+1, l+33) stay in place?
+        const bool nx0 = l < 31 ? ((b0 >> (l + 1)) & 1u) != 0 : (b1 & 1u) != 0;
+        const bool nx1 = l < 31 ? ((b1 >> (l + 1)) & 1u) != 0 : false;
+        __syncwarp();
+        if (ok0) {
+            sd.px()[i0 + 1] = p0;
+            sd.qty()[i0 + 1] = q0;
+            sd.oid()[i0 + 1] = o0;
+            sd.tid()[i0 + 1] = t0;
+            sd.tm()[i0 + 1] = e0;
+        }
+        if (ok1) {
+            sd.px()[i1 + 1] = p1;
+            sd.qty()[i1 + 1] = q1;
+            sd.oid()[i1 + 1] = o1;
+            sd.tid()[i1 + 1] = t1;
+            sd.tm()[i1 + 1] = e1;
+        }
+        const bool place0 = ok0 && !nx0, place1 = ok1 && !nx1;
+        if (place0 || place1 || (l == 0 && b0 == 0u)) {
+            const int at = place1 ? i1 : (place0 ? i0 : n);
+            sd.px()[at] = P;
+            sd.qty()[at] = Q;
+            sd.oid()[at] = oid;
+            sd.tid()[at] = tid;
+            sd.tm()[at] = tnew;
+        }
+    } else {
+        // a deep insert: count the orders at least as good below the window
+        int p = 64;
+#pragma unroll 1
+        for (int top = n - 64; top > 0; top -= 64) {
+            const int j0 = top - 1 - l, j1 = top - 33 - l;
+            const bool c0 = j0 >= 0 && at_least<X>(sd.px()[j0 >= 0 ? j0 : 0], P);
+            const bool c1 = j1 >= 0 && at_least<X>(sd.px()[j1 >= 0 ? j1 : 0], P);
+            const int c = __popc(__ballot_sync(kFull, c0)) + __popc(__ballot_sync(kFull, c1));
+            p += c;
+            if (c < 64) break;
+        }
+        __syncwarp();
+        const int lo = n - p;
+        g_move_up<K>(sd, lo, n);
+        if (l == 0) {
+            sd.px()[lo] = P;
+            sd.qty()[lo] = Q;
+            sd.oid()[lo] = oid;
+            sd.tid()[lo] = tid;
+            sd.tm()[lo] = tnew;
+        }
     }
     n += 1;
     ctr.rested += 1;
