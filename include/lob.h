@@ -235,6 +235,18 @@ int lob_process_host(lob_ctx* ctx, const lob_msg_t* h_msgs, int64_t msgs_per_boo
 int lob_get_levels(lob_ctx* ctx, int32_t depth, int32_t* d_bid_px, int32_t* d_bid_qty,
                    int32_t* d_ask_px, int32_t* d_ask_qty, void* stream);
 
+/* The same levels for the books listed in d_book_ids (int32[n_active],
+ * device, caller-owned; e.g. the ids just passed to lob_process_batch), each
+ * written to its own row of the int32[n_books][depth] outputs; the rows of
+ * books not listed are left as they are.  An id outside 0..n_books-1 sets
+ * LOB_STATUS_BAD_BOOK and is skipped.  n_active 0 launches nothing (then
+ * d_book_ids may be NULL; otherwise NULL is LOB_E_INVAL).  This is
+ * the per-step level output of a batch in which only some books advanced (a
+ * serving tick), at the cost of those books alone. */
+int lob_get_levels_books(lob_ctx* ctx, const int32_t* d_book_ids, int32_t n_active,
+                         int32_t depth, int32_t* d_bid_px, int32_t* d_bid_qty,
+                         int32_t* d_ask_px, int32_t* d_ask_qty, void* stream);
+
 /* Trade logs: d_out is lob_trade_t[n_books][trade_capacity] in execution
  * order, entries past the stored count all -1; d_counts int64[n_books] is the
  * number of trades executed (may exceed trade_capacity).  Either pointer may

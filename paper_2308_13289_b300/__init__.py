@@ -139,6 +139,13 @@ def lob_get_levels(h, depth, bid_px, bid_qty, ask_px, ask_qty, stream=None):
                                _ptr(ask_qty), _stream(stream)), "lob_get_levels")
 
 
+def lob_get_levels_books(h, book_ids, n_active, depth, bid_px, bid_qty, ask_px, ask_qty,
+                         stream=None):
+    check(lib().lob_get_levels_books(h, _ptr(book_ids), n_active, depth, _ptr(bid_px),
+                                     _ptr(bid_qty), _ptr(ask_px), _ptr(ask_qty),
+                                     _stream(stream)), "lob_get_levels_books")
+
+
 def lob_get_trades(h, out, counts, stream=None):
     check(lib().lob_get_trades(h, _ptr(out), _ptr(counts), _stream(stream)), "lob_get_trades")
 
@@ -312,6 +319,17 @@ class Engine:
         out = [torch.empty((self.n_books, depth), dtype=torch.int32, device="cuda")
                for _ in range(4)]
         lob_get_levels(self.h, depth, *out, stream=self.stream)
+        return tuple(out)
+
+    def levels_of(self, book_ids, depth: int, out=None):
+        """Levels of the listed books (int32 CUDA tensor of ids) written to
+        their rows of `out` (four int32 [n_books, depth] tensors, allocated
+        filled with -7 when None); other rows are left as they are."""
+        if out is None:
+            out = [torch.full((self.n_books, depth), -7, dtype=torch.int32, device="cuda")
+                   for _ in range(4)]
+        lob_get_levels_books(self.h, book_ids, int(book_ids.numel()), depth, *out,
+                             stream=self.stream)
         return tuple(out)
 
     def trades(self):

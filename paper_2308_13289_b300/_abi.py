@@ -37,6 +37,7 @@ SIGNATURES = {
     "lob_process_batch_l1": (ctypes.c_int, [vp, vp, vp, vp, i32, vp, vp]),
     "lob_clear_trades": (ctypes.c_int, [vp, vp]),
     "lob_get_levels": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp]),
+    "lob_get_levels_books": (ctypes.c_int, [vp, vp, i32, i32, vp, vp, vp, vp, vp]),
     "lob_get_trades": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_get_book": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),
     "lob_set_book": (ctypes.c_int, [vp, vp, vp, vp, vp, vp, vp, vp]),

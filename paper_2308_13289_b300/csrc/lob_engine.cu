@@ -64,17 +64,25 @@ cudaError_t lob_raise_smem_limit(const void* fn, int bytes)
 
 namespace {
 
-// Top `depth` levels of every book (warp per book, both sides).
+// Top `depth` levels (warp per book, both sides) of every book, or of the
+// `n_items` books listed in `book_ids` (an id outside 0..n_books-1 sets
+// LOB_STATUS_BAD_BOOK and is skipped).
 template <int K>
 __global__ void k_levels(const char* __restrict__ state, const int32_t* __restrict__ counts,
-                         int32_t n_books, int32_t depth, int32_t* bid_px, int32_t* bid_qty,
+                         int32_t n_books, const int32_t* __restrict__ book_ids, int32_t n_items,
+                         int32_t* status, int32_t depth, int32_t* bid_px, int32_t* bid_qty,
                          int32_t* ask_px, int32_t* ask_qty)
 {
     __shared__ unsigned long long lq[8][128];
     __shared__ int32_t lp[8][64];
     const int l = lane_id(), w = threadIdx.x >> 5;
-    const int b = blockIdx.x * (blockDim.x >> 5) + w;
-    if (b >= n_books) return;
+    const int item = blockIdx.x * (blockDim.x >> 5) + w;
+    if (item >= n_items) return;
+    const int b = book_ids ? book_ids[item] : item;
+    if (b < 0 || b >= n_books) {
+        if (l == 0) atomicOr(status, LOB_STATUS_BAD_BOOK);
+        return;
+    }
     for (int x = 0; x < 2; ++x) {
         const char* side = state + (int64_t)b * Geo<K>::BOOK_BYTES + x * Geo<K>::SIDE_BYTES;
         const int32_t* px = reinterpret_cast<const int32_t*>(side + Geo<K>::PX);
@@ -751,23 +759,45 @@ int lob_clear_trades(lob_ctx* c, void* stream)
     default: { constexpr int KK = 16; CALL; } break;  \
     }
 
+static int launch_levels(lob_ctx* c, const int32_t* d_book_ids, int32_t n_items, int32_t depth,
+                         int32_t* d_bid_px, int32_t* d_bid_qty, int32_t* d_ask_px,
+                         int32_t* d_ask_qty, void* stream, const char* who)
+{
+    if (!c || depth < 1 || depth > 64 || !d_bid_px || !d_bid_qty || !d_ask_px || !d_ask_qty ||
+        n_items < 0 || (n_items > 0 && d_book_ids == nullptr && n_items != c->cfg.n_books)) {
+        lob_set_error("%s: invalid argument (depth=%d, n_active=%d)", who, depth, n_items);
+        return LOB_E_INVAL;
+    }
+    if (n_items == 0) return LOB_OK;
+    const int wpb = 8;
+    dim3 grid((n_items + wpb - 1) / wpb), block(32 * wpb);
+    cudaStream_t s = (cudaStream_t)stream;
+    LOB_DISPATCH_K(c->K, (k_levels<KK><<<grid, block, 0, s>>>(
+                             c->d_state, c->d_counts, c->cfg.n_books, d_book_ids, n_items,
+                             c->d_status, depth, d_bid_px, d_bid_qty, d_ask_px, d_ask_qty)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return lob_cuda_fail(e, who);
+    c->launches += 1;
+    return LOB_OK;
+}
+
 int lob_get_levels(lob_ctx* c, int32_t depth, int32_t* d_bid_px, int32_t* d_bid_qty,
                    int32_t* d_ask_px, int32_t* d_ask_qty, void* stream)
 {
-    if (!c || depth < 1 || depth > 64 || !d_bid_px || !d_bid_qty || !d_ask_px || !d_ask_qty) {
-        lob_set_error("lob_get_levels: invalid argument (depth=%d)", depth);
+    return launch_levels(c, nullptr, c ? c->cfg.n_books : 0, depth, d_bid_px, d_bid_qty,
+                         d_ask_px, d_ask_qty, stream, "lob_get_levels");
+}
+
+int lob_get_levels_books(lob_ctx* c, const int32_t* d_book_ids, int32_t n_active, int32_t depth,
+                         int32_t* d_bid_px, int32_t* d_bid_qty, int32_t* d_ask_px,
+                         int32_t* d_ask_qty, void* stream)
+{
+    if (!d_book_ids && n_active != 0) {
+        lob_set_error("lob_get_levels_books: d_book_ids is NULL");
         return LOB_E_INVAL;
     }
-    const int wpb = 8;
-    dim3 grid((c->cfg.n_books + wpb - 1) / wpb), block(32 * wpb);
-    cudaStream_t s = (cudaStream_t)stream;
-    LOB_DISPATCH_K(c->K, (k_levels<KK><<<grid, block, 0, s>>>(c->d_state, c->d_counts,
-                                                              c->cfg.n_books, depth, d_bid_px,
-                                                              d_bid_qty, d_ask_px, d_ask_qty)));
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return lob_cuda_fail(e, "lob_get_levels");
-    c->launches += 1;
-    return LOB_OK;
+    return launch_levels(c, d_book_ids, n_active, depth, d_bid_px, d_bid_qty, d_ask_px,
+                         d_ask_qty, stream, "lob_get_levels_books");
 }
 
 int lob_get_trades(lob_ctx* c, lob_trade_t* d_out, int64_t* d_counts, void* stream)

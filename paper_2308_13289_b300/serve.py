@@ -17,8 +17,9 @@ batch that is already running.
 
 Every tick advances ALL admitted episodes by one step.  Per capacity class:
 one generator launch writes the active slots' windows on the pool's generator
-stream, one lob_process_batch launch applies them and one lob_get_levels
-launch reports the levels on the pool's processing stream.  The windows are
+stream, one lob_process_batch launch applies them and one
+lob_get_levels_books launch reports the levels of the same slots (not of the
+whole pool) on the pool's processing stream.  The windows are
 double-buffered, so the generator produces tick k+1 while tick k is being
 processed; the classes run on their own streams and overlap on the device.
 
@@ -46,7 +47,7 @@ import torch
 
 import lobgen
 
-from . import N_COUNTERS, Engine, lib, lob_get_levels
+from . import N_COUNTERS, Engine, lib
 
 MSG_BYTES = 32
 RING = 8  # ticks the host may run ahead of the GPU
@@ -270,8 +271,8 @@ class _Pool:
             raise RuntimeError("lob_reset_books failed")
         if lb.lob_process_batch(h, self.a_win[k], ap["off"], ap["ids"], n, self.h_ps) != 0:
             raise RuntimeError("lob_process_batch failed")
-        if lb.lob_get_levels(h, self.depth, *self.a_levels, self.h_ps) != 0:
-            raise RuntimeError("lob_get_levels failed")
+        if lb.lob_get_levels_books(h, ap["ids"], n, self.depth, *self.a_levels, self.h_ps) != 0:
+            raise RuntimeError("lob_get_levels_books failed")
         if self.collect:
             lb.lob_get_trades(h, None, self.a_tcount, self.h_ps)
         if timing:
