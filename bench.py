@@ -657,6 +657,52 @@ def run_uneven(args, rank):
     return res
 
 
+def env_oracle_check(w, params, ids, got, draws=None, actions=None, final=None, obs=None,
+                     chunk=1024):
+    """The oracle's environments (oracle.EnvOracle, all host threads) replay
+    the episode of every environment, `chunk` environments at a time, from the
+    host copy of the same seeded streams; every step's reward (by its bits),
+    fills and four level arrays are compared with `got` (host arrays
+    [steps, n, ...]); so are, when given, the final books and agent state
+    (`final`) and, for the policy form (`actions`), the last step's
+    observation (`obs`).  Returns the verdict (and the observation's)."""
+    import lobgen
+    import oracle
+    steps, n = got["reward"].shape
+    per = w["msgs_per_step"]
+    ok, ok_obs = True, True
+    for c0 in range(0, n, chunk):
+        sel = np.arange(c0, min(n, c0 + chunk))
+        hm, _ = lobgen.generate(params, [steps * per] * len(sel), stream_ids=ids[sel])
+        rows = hm.reshape(len(sel), steps, per)
+        offs = np.arange(0, len(sel) * per + 1, per)
+        oenv = oracle.EnvOracle(len(sel), w["capacity"], 4096, n_steps=steps)
+        tr = None
+        for t in range(steps):
+            stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
+            if actions is None:
+                r_, lv, f_ = oenv.step(stp, offs, draws[t, sel], t)
+            else:
+                r_, lv, f_, tr = oenv.step(stp, offs, None, t, l1=True, actions=actions[t, sel])
+            ok &= got["reward"][t, sel].tobytes() == r_.tobytes()
+            ok &= np.array_equal(got["fills"][t, sel], f_)
+            for k, x in zip(("bid_px", "bid_qty", "ask_px", "ask_qty"), lv):
+                ok &= np.array_equal(got[k][t, sel], x)
+        if final is not None:
+            ost, op0 = oenv.state()
+            ok &= np.array_equal(final["state"][sel], ost)
+            ok &= final["p_init"][sel].tobytes() == op0.tobytes()
+            for k, v in oenv.books.book().items():
+                ok &= np.array_equal(final["books"][k][sel], v)
+        if obs is not None:
+            t_init = rows[:, 0, 0]["time_ns"].astype(np.int64)
+            ok_obs &= oenv.observe(tr, per, t_init).tobytes() == obs[sel].tobytes()
+        del oenv, hm, rows
+        if not ok:
+            break
+    return (ok, ok_obs) if obs is not None else ok
+
+
 def run_rl(args, rank, name="rl_exec_8192x400"):
     """8,192 execution environments x 400 steps x 100 data messages: one launch
     per step, the same 400 launches replayed from a CUDA graph, and one
@@ -756,6 +802,9 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
     res["graph_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snapshot()))
     del g
     std_out = {k: v.cpu().numpy() for k, v in out.items()}  # the stand-in agent's episode
+    st_, p0_ = env.state()
+    std_final = dict(state=st_.cpu().numpy(), p_init=p0_.cpu().numpy(),
+                     books={k: v.cpu().numpy() for k, v in e.book().items()})
     res["overflow"] = overflow_stats(e)
     # policy loop (Sec. 5.2.2-5.2.3): every step acts on four sizes and ends
     # with the step's level-1 trace and the observation vector, as a policy in
@@ -799,40 +848,20 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
                      "launches": (1 if name == "persistent_episode" else
                                   2 * steps if name.startswith("policy") else steps)}
     if rank == 0:
-        sample = np.array([0, 1, 2, n // 2, n - 1])
-        hm, hoff = lobgen.generate(params, [steps * per] * len(sample), stream_ids=ids[sample])
-        hd = lobgen.agent_draws(w["seed"] + 1, n, steps)[:, sample]
-        oenv = oracle.EnvOracle(len(sample), w["capacity"], 4096, n_steps=steps)
-        rows = hm.reshape(len(sample), steps, per)
-        ok = True
-        rew, fills, lvb = std_out["reward"], std_out["fills"], std_out["bid_px"]
-        for t in range(steps):
-            stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
-            r_, lv, f_ = oenv.step(stp, np.arange(0, len(sample) * per + 1, per), hd[t], t)
-            ok &= rew[t, sample].tobytes() == r_.tobytes()
-            ok &= np.array_equal(fills[t, sample], f_)
-            ok &= np.array_equal(lvb[t, sample], lv[0])
-        res["parity"] = {"envs_checked": int(len(sample)), "steps_checked": steps,
-                         "bit_exact": bool(ok)}
-        # the policy form's last run (still in `out`): rewards, fills, best
-        # bids per step and the final observation
-        oenv = oracle.EnvOracle(len(sample), w["capacity"], 4096, n_steps=steps)
-        ha = act.cpu().numpy()[:, sample]
-        t_init = rows[:, 0, 0]["time_ns"].astype(np.int64)
-        rew = out["reward"].cpu().numpy()
-        fills = out["fills"].cpu().numpy()
-        lvb = out["bid_px"].cpu().numpy()
-        ok = True
-        for t in range(steps):
-            stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
-            r_, lv, f_, tr = oenv.step(stp, np.arange(0, len(sample) * per + 1, per), None, t,
-                                       l1=True, actions=ha[t])
-            ok &= rew[t, sample].tobytes() == r_.tobytes()
-            ok &= np.array_equal(fills[t, sample], f_)
-            ok &= np.array_equal(lvb[t, sample], lv[0])
-        ok_obs = oenv.observe(tr, per, t_init).tobytes() == obs.cpu().numpy()[sample].tobytes()
-        res["policy_parity"] = {"envs_checked": int(len(sample)), "steps_checked": steps,
-                                "bit_exact": bool(ok), "final_observation_bit_exact": bool(ok_obs)}
+        # every environment, every step, against the oracle's environments
+        hd = lobgen.agent_draws(w["seed"] + 1, n, steps)
+        t0 = time.time()
+        ok = env_oracle_check(w, params, ids, std_out, draws=hd, final=std_final)
+        res["parity"] = {"envs_checked": n, "steps_checked": steps, "bit_exact": bool(ok),
+                         "compared": "every step's reward bits, fills and four level arrays; "
+                                     "final books and agent state",
+                         "oracle_s": round(time.time() - t0, 1)}
+        t0 = time.time()
+        ok, ok_obs = env_oracle_check(w, params, ids, {k: v.cpu().numpy() for k, v in out.items()},
+                                      actions=act.cpu().numpy(), obs=obs.cpu().numpy())
+        res["policy_parity"] = {"envs_checked": n, "steps_checked": steps, "bit_exact": bool(ok),
+                                "final_observation_bit_exact": bool(ok_obs),
+                                "oracle_s": round(time.time() - t0, 1)}
     env.close()
     e.close()
     del dm, out

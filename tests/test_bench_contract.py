@@ -10,6 +10,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -65,3 +66,65 @@ def test_issue_roofline_arithmetic():
     assert abs(r["frac"] - 118.0 * 3.89e9 / (148 * 4 * 2032e6)) < 1e-4
     assert abs(r["peak"] - 148 * 4 * 2.032) < 0.01
     assert bench.issue_roofline(None, 1.0, 2032.0, "none", sms=148)["frac"] is None
+
+
+def _env_episode(n, steps, w, params, ids, draws=None, actions=None):
+    """Host arrays of one episode of the oracle's environments (the shape of
+    the device outputs the bench compares) and its final books and state."""
+    import lobgen
+    import oracle
+    per = w["msgs_per_step"]
+    hm, _ = lobgen.generate(params, [steps * per] * n, stream_ids=ids)
+    rows = hm.reshape(n, steps, per)
+    oenv = oracle.EnvOracle(n, w["capacity"], 4096, n_steps=steps)
+    got = dict(reward=[], bid_px=[], bid_qty=[], ask_px=[], ask_qty=[], fills=[])
+    tr = None
+    for t in range(steps):
+        stp = np.ascontiguousarray(rows[:, t, :]).reshape(-1)
+        offs = np.arange(0, n * per + 1, per)
+        if actions is None:
+            r_, lv, f_ = oenv.step(stp, offs, draws[t], t)
+        else:
+            r_, lv, f_, tr = oenv.step(stp, offs, None, t, l1=True, actions=actions[t])
+        got["reward"].append(r_)
+        got["fills"].append(f_)
+        for k, x in zip(("bid_px", "bid_qty", "ask_px", "ask_qty"), lv):
+            got[k].append(x)
+    got = {k: np.stack(v) for k, v in got.items()}
+    st, p0 = oenv.state()
+    final = dict(state=st, p_init=p0, books=oenv.books.book())
+    obs = oenv.observe(tr, per, rows[:, 0, 0]["time_ns"].astype(np.int64)) if tr is not None \
+        else None
+    return got, final, obs
+
+
+def test_env_oracle_check_passes_the_oracles_episode_and_fails_a_changed_one():
+    """The bench's all-environments RL parity check, chunked (3 chunks, the
+    last ragged): equal outputs pass; one reward bit, one fill or one final
+    book entry changed fails; the policy form's observation is checked too."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import lobgen
+    w = dict(lobgen.WORKLOADS["rl_exec_8192x400"])
+    n, steps = 9, 12
+    params = lobgen.make_params(w["seed"], w["mid_walk"])
+    ids = np.arange(n, dtype=np.uint64)
+    draws = lobgen.agent_draws(w["seed"] + 1, n, steps)
+    got, final, _ = _env_episode(n, steps, w, params, ids, draws=draws)
+    assert bench.env_oracle_check(w, params, ids, got, draws=draws, final=final, chunk=4)
+    bad = {k: v.copy() for k, v in got.items()}
+    bad["reward"][steps - 1, n - 1] = np.nextafter(bad["reward"][steps - 1, n - 1], np.float32(1e9))
+    assert not bench.env_oracle_check(w, params, ids, bad, draws=draws, chunk=4)
+    bad = {k: v.copy() for k, v in got.items()}
+    bad["fills"][3, 5, 0] += 1
+    assert not bench.env_oracle_check(w, params, ids, bad, draws=draws, chunk=4)
+    fb = dict(final, books={k: v.copy() for k, v in final["books"].items()})
+    fb["books"]["qty"][8, 0, 0] += 1
+    assert not bench.env_oracle_check(w, params, ids, got, draws=draws, final=fb, chunk=4)
+    rng = np.random.default_rng(3)
+    act = (rng.random((steps, n, 4)) * 4.0).astype(np.float32)
+    got, _, obs = _env_episode(n, steps, w, params, ids, actions=act)
+    assert bench.env_oracle_check(w, params, ids, got, actions=act, obs=obs, chunk=4) == (True, True)
+    ob = obs.copy()
+    ob[7, 0] += 1.0
+    assert bench.env_oracle_check(w, params, ids, got, actions=act, obs=ob, chunk=4) == (True, False)
