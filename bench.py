@@ -457,6 +457,48 @@ def _events():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
+def replay_oracle_check(e, params, ids, counts, cap, tcap, depth=10, chunk=4096, logs=4):
+    """Every book of a replay run against the oracle replaying the same seeded
+    streams (host copies, all host threads), `chunk` books at a time: the
+    canonical books, top `depth` levels, counters and trade counts of every
+    book, and the whole trade logs of the first `logs` books of each chunk.
+    Returns (verdict, oracle seconds)."""
+    import torch
+
+    import lobgen
+    import oracle
+    n = len(counts)
+    bk = {k: v.cpu().numpy() for k, v in e.book().items()}
+    lv = [x.cpu().numpy() for x in e.levels(depth)]
+    ctr = e.stats()[0].cpu().numpy()
+    gt, gc = e.trades()
+    tc = gc.cpu().numpy()
+    ok, secs = True, 0.0
+    for c0 in range(0, n, chunk):
+        sel = np.arange(c0, min(n, c0 + chunk))
+        hm, hoff = lobgen.generate(params, counts[sel], stream_ids=ids[sel])
+        o = oracle.Oracle(len(sel), cap, tcap)
+        t = time.perf_counter()
+        o.process(hm, hoff)
+        secs += time.perf_counter() - t
+        for k, v in o.book().items():
+            ok &= np.array_equal(bk[k][sel], v)
+        for g, x in zip(lv, o.levels(depth)):
+            ok &= np.array_equal(g[sel], x)
+        ok &= np.array_equal(ctr[sel], o.counters())
+        ot, oc = o.trades()
+        ok &= np.array_equal(tc[sel], oc)
+        m = min(logs, len(sel))
+        ok &= np.array_equal(gt[c0:c0 + m].cpu().numpy(),
+                             ot[:m].view(np.int32).reshape(m, tcap, 8))
+        del o, hm, hoff, ot
+        if not ok:
+            break
+    del gt
+    torch.cuda.empty_cache()
+    return bool(ok), secs
+
+
 def run_sweep(args, rank, inst_per_msg=None, clk=None, sizes=(1024, 4096, 16384), per=10_000):
     """The replay workload's generator at 10^4 messages per book and a growing
     number of books (persistent form, autotuned shape): where the kernel
@@ -465,7 +507,6 @@ def run_sweep(args, rank, inst_per_msg=None, clk=None, sizes=(1024, 4096, 16384)
     import torch
 
     import lobgen
-    import oracle
     import paper_2308_13289_b300 as eng
     from paper_2308_13289_b300 import autotune
     w = lobgen.WORKLOADS["replay_1024x10k"]
@@ -510,14 +551,8 @@ def run_sweep(args, rank, inst_per_msg=None, clk=None, sizes=(1024, 4096, 16384)
                                        "headline record's instructions per message"),
                "device_status": int(st.item())}
         if rank == 0:
-            sample = np.array([0, n // 3, n - 1])
-            hm, hoff = lobgen.generate(params, [per] * len(sample), stream_ids=ids[sample])
-            o = oracle.Oracle(len(sample), cap, tcap)
-            o.process(hm, hoff)
-            bk = e.book()
-            ok = all(np.array_equal(bk[k][sample].cpu().numpy(), v) for k, v in o.book().items())
-            ok &= np.array_equal(ctr[sample].cpu().numpy(), o.counters())
-            row["parity"] = {"books_checked": int(len(sample)), "bit_exact": bool(ok)}
+            ok, secs = replay_oracle_check(e, params, ids, np.full(n, per, np.int64), cap, tcap)
+            row["parity"] = {"books_checked": n, "bit_exact": ok, "oracle_s": round(secs, 2)}
         res["n%d" % n] = row
         e.close()
         del dm, doff
@@ -592,7 +627,6 @@ def run_uneven(args, rank):
     import torch
 
     import lobgen
-    import oracle
     import paper_2308_13289_b300 as eng
     w = lobgen.WORKLOADS["uneven_4096_lognormal"]
     n = w["n_books"]
@@ -640,16 +674,10 @@ def run_uneven(args, rank):
         ms = float(np.mean(times))
         res[order] = {"ms_per_step": round(ms, 4), "msgs_per_s": round(res["messages"] / ms * 1e3, 1)}
         if order == "longest_first" and rank == 0:
-            # parity on a sample of books (oracle replays their own streams)
-            sample = np.array(sorted(set([0, 1, n - 1] + list(perm[:3]) + list(perm[-3:]))))
-            hm, hoff = lobgen.generate(params, counts[sample], stream_ids=ids[sample])
-            o = oracle.Oracle(len(sample), w["capacity"], tcap)
-            o.process(hm, hoff)
-            bk = e.book()
-            ok = all(np.array_equal(bk[k][sample].cpu().numpy(), v) for k, v in o.book().items())
-            ctr, st = e.stats()
-            ok &= np.array_equal(ctr[sample].cpu().numpy(), o.counters())
-            res["parity"] = {"books_checked": int(len(sample)), "bit_exact": bool(ok),
+            # every book against the oracle replaying its own stream
+            ok, secs = replay_oracle_check(e, params, ids, counts, w["capacity"], tcap)
+            _, st = e.stats()
+            res["parity"] = {"books_checked": n, "bit_exact": ok, "oracle_s": round(secs, 2),
                              "device_status": int(st.item())}
             res["overflow"] = overflow_stats(e)
         e.close()

@@ -128,3 +128,57 @@ def test_env_oracle_check_passes_the_oracles_episode_and_fails_a_changed_one():
     ob = obs.copy()
     ob[7, 0] += 1.0
     assert bench.env_oracle_check(w, params, ids, got, actions=act, obs=ob, chunk=4) == (True, False)
+
+
+class _OracleAsEngine:
+    """The outputs the bench reads from an engine, served by an oracle run
+    (CPU torch tensors), optionally with one value changed."""
+
+    def __init__(self, o, depth=10, change=None):
+        import torch
+        self.bk = {k: torch.from_numpy(v.copy()) for k, v in o.book().items()}
+        self.lv = [torch.from_numpy(x.copy()) for x in o.levels(depth)]
+        self.ctr = torch.from_numpy(o.counters().copy())
+        tr, cnt = o.trades()
+        self.tr = torch.from_numpy(tr.view(np.int32).reshape(o.n_books, o.trade_capacity, 8).copy())
+        self.cnt = torch.from_numpy(cnt.copy())
+        if change == "level":
+            self.lv[3][5, 0] += 1
+        elif change == "trade_log":
+            self.tr[1, 0, 1] += 1
+        elif change == "count":
+            self.cnt[6] += 1
+
+    def book(self):
+        return self.bk
+
+    def levels(self, depth):
+        return self.lv
+
+    def stats(self):
+        import torch
+        return self.ctr, torch.zeros(1, dtype=torch.int32)
+
+    def trades(self):
+        return self.tr, self.cnt
+
+
+@pytest.mark.parametrize("change", [None, "level", "trade_log", "count"])
+def test_replay_oracle_check_every_book_in_chunks(change):
+    """The bench's every-book replay check (3 chunks, the last ragged): the
+    oracle's own outputs pass; a changed level, trade-log entry of a checked
+    log or trade count fails."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import lobgen
+    import oracle
+    n, cap, tcap = 7, 100, 400
+    params = lobgen.make_params(5, "pm1")
+    ids = np.arange(n, dtype=np.uint64)
+    counts = np.array([300, 10, 700, 0, 250, 500, 90], dtype=np.int64)
+    m, off = lobgen.generate(params, counts, stream_ids=ids)
+    o = oracle.Oracle(n, cap, tcap)
+    o.process(m, off)
+    ok, _ = bench.replay_oracle_check(_OracleAsEngine(o, change=change), params, ids, counts, cap,
+                                      tcap, chunk=3, logs=2)
+    assert ok == (change is None)
