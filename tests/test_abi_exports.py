@@ -54,3 +54,9 @@ def test_cpu_only_calls_fail_cleanly(lib):
     assert lib.lob_create(None, None, None) == -1
     lib.lob_last_error.restype = ctypes.c_char_p
     assert b"null" in lib.lob_last_error()
+    # argument errors are caught on the host before any launch
+    lib.lob_get_levels_books.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                         ctypes.c_int32] + [ctypes.c_void_p] * 5
+    one = ctypes.c_void_p(16)
+    assert lib.lob_get_levels_books(None, one, 1, 10, one, one, one, one, None) == -1
+    assert b"lob_get_levels_books" in lib.lob_last_error()
