@@ -471,6 +471,93 @@ int lob_process_streams_static(const lob_msg_t* d_msgs, const int64_t* d_offsets
 
 /* ------------------------------------------------------------------ tuning */
 
+/* ---------------------------------------------------- serving tick executor */
+
+/* Continuous batching of simulation episodes over the books of one context
+ * (no counterpart in the paper; each tick applies one step of every running
+ * episode, the replay step of Sec. 5.1.1 / 5.1.3): a book per slot, a running
+ * episode per occupied slot, advancing one step per tick.  A tick produces the
+ * occupied slots' windows of data messages with the caller's device generator
+ * on gen_stream, then, on proc_stream, resets the books of episodes admitted
+ * since the last tick, applies the windows (lob_process_batch) and writes the
+ * levels of the advanced books (lob_get_levels_books).  The upload of a tick
+ * (its offsets, slots and restarts) goes through a ring of `ring` pinned host
+ * buffers, so the host may run up to `ring` ticks ahead of the GPU; the windows
+ * alternate between two buffers.  Host code; one thread per executor. */
+
+/* The device generator, called on gen_stream: init resets the state of n
+ * slots (d_slots int32[n]) to the streams d_stream_ids (uint64[n]); advance
+ * writes, for n slots, d_counts[i] messages of slot d_slots[i]'s stream into
+ * d_out (lob_msg_t) at d_offsets[i].  Both return 0 on success. */
+typedef int (*lob_gen_init_fn)(const void* params, int32_t n, const int32_t* d_slots,
+                               const uint64_t* d_stream_ids, void* d_states, void* stream);
+typedef int (*lob_gen_advance_fn)(const void* params, const void* d_geo_px,
+                                  const void* d_geo_q, int32_t n, const int32_t* d_slots,
+                                  void* d_states, void* d_pools, const int64_t* d_counts,
+                                  const int64_t* d_offsets, void* d_out, void* stream);
+
+typedef struct {
+    lob_ctx* engine;            /* the books: n_books == slots                       */
+    const void* gen_params;     /* host, the generator's parameters (caller keeps)   */
+    lob_gen_init_fn gen_init;
+    lob_gen_advance_fn gen_advance;
+    const void* d_geo_px;       /* generator tables and per-slot state (device,      */
+    const void* d_geo_q;        /*   caller-owned, passed through to the generator)  */
+    void* d_gen_states;
+    void* d_gen_pools;
+    void* d_win0;               /* two window buffers, lob_msg_t[slots * max_msgs]   */
+    void* d_win1;
+    int32_t* d_bid_px;          /* levels of the advanced books, int32[slots][depth] */
+    int32_t* d_bid_qty;
+    int32_t* d_ask_px;
+    int32_t* d_ask_qty;
+    int64_t* d_trade_counts;    /* int64[slots], written by ticks with `collect`     */
+    void* proc_stream;          /* cudaStream_t, caller-owned                        */
+    void* gen_stream;
+    int32_t slots;
+    int32_t max_msgs;           /* messages per step, at most                        */
+    int32_t depth;              /* levels 1..64                                      */
+    int32_t ring;               /* ticks the host may run ahead, 1..64               */
+} lob_serve_desc;
+
+typedef struct lob_serve lob_serve;
+
+/* Allocates the executor (two device upload buffers, the pinned ring, events);
+ * every pointer of the descriptor must be non-null.  LOB_E_INVAL on a bad
+ * descriptor, LOB_E_NOMEM / LOB_E_CUDA on allocation failure. */
+int lob_serve_create(lob_serve** out, const lob_serve_desc* desc);
+
+/* Admit an episode of n_steps steps of msgs_per_step (0..max_msgs) messages
+ * from generator stream stream_id into a free slot (*slot_out); its
+ * book and generator state are reset at the next tick.  LOB_E_STATE with
+ * *slot_out = -1 when every slot is occupied. */
+int lob_serve_admit(lob_serve* s, uint64_t stream_id, int64_t n_steps, int32_t msgs_per_step,
+                    int32_t* slot_out);
+
+/* One step of every occupied slot, issued asynchronously (waits only for the
+ * ring buffer it reuses).  Outputs: *n_active occupied slots advanced (listed
+ * in ascending order in h_active, int32[slots], when non-null), *n_finished
+ * slots whose episode took its last step (h_finished, int32[slots]; they are
+ * free from now on, their books valid until a later admission resets them in
+ * stream order), *n_msgs messages.  timing != 0 records the tick's processing
+ * and generation times (lob_serve_timings); collect != 0 also writes every
+ * book's trade count into d_trade_counts.  No occupied slot: nothing issued. */
+int lob_serve_tick(lob_serve* s, int32_t timing, int32_t collect, int32_t* h_active,
+                   int32_t* n_active, int32_t* h_finished, int32_t* n_finished,
+                   int64_t* n_msgs);
+
+/* Waits for every tick issued so far; *count = timed ticks recorded.  When cap
+ * >= *count, copies, oldest first, each tick's processing time (ms, from its
+ * windows being ready to its levels written, on proc_stream), generation time
+ * (ms, on gen_stream) and slots advanced, and clears the record; otherwise
+ * copies nothing. */
+int lob_serve_timings(lob_serve* s, float* proc_ms, float* gen_ms, int32_t* n_in_tick,
+                      int32_t cap, int32_t* count);
+
+/* Waits for the ticks in flight and frees the executor (not the caller's
+ * buffers, streams or context).  NULL is a no-op. */
+int lob_serve_destroy(lob_serve* s);
+
 /* Launch shape of the processing kernel: warps (= books in flight) per CTA
  * (1..16; 1..8 for capacity > 128), messages per staged chunk (8..1024,
  * multiple of 8), and CTAs per SM for the persistent grid (0 = as many as

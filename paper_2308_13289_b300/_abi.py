@@ -25,6 +25,15 @@ class LobEnvConfig(ctypes.Structure):
                 ("passive_ticks", i32), ("tick_size", i32)]
 
 
+class LobServeDesc(ctypes.Structure):
+    """lob_serve_desc: the generator's functions travel as plain addresses."""
+    _fields_ = [(name, vp) for name in (
+        "engine", "gen_params", "gen_init", "gen_advance", "d_geo_px", "d_geo_q",
+        "d_gen_states", "d_gen_pools", "d_win0", "d_win1", "d_bid_px", "d_bid_qty",
+        "d_ask_px", "d_ask_qty", "d_trade_counts", "proc_stream", "gen_stream")] + \
+        [("slots", i32), ("max_msgs", i32), ("depth", i32), ("ring", i32)]
+
+
 # name -> (restype, argtypes); every symbol of include/lob.h
 SIGNATURES = {
     "lob_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(LobConfig), vp]),
@@ -56,6 +65,11 @@ SIGNATURES = {
     "lob_literal_process": (ctypes.c_int, [vp, vp, i32, i32, i32, i32, i32] + [vp] * 8 + [vp]),
     "lob_env_get_state": (ctypes.c_int, [vp, vp, vp, vp]),
     "lob_env_segments": (ctypes.c_int32, [vp]),
+    "lob_serve_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(LobServeDesc)]),
+    "lob_serve_admit": (ctypes.c_int, [vp, ctypes.c_uint64, i64, i32, ctypes.POINTER(i32)]),
+    "lob_serve_tick": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
+    "lob_serve_timings": (ctypes.c_int, [vp, vp, vp, vp, i32, ctypes.POINTER(i32)]),
+    "lob_serve_destroy": (ctypes.c_int, [vp]),
     "lob_last_error": (ctypes.c_char_p, []),
     "lob_abi_version": (ctypes.c_int, []),
 }

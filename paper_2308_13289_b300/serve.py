@@ -15,13 +15,16 @@ HBM budget beside the episodes already running.  Episodes that finish free
 their slot and their footprint in the same tick, so later arrivals join a
 batch that is already running.
 
-Every tick advances ALL admitted episodes by one step.  Per capacity class:
-one generator launch writes the active slots' windows on the pool's generator
-stream, one lob_process_batch launch applies them and one
-lob_get_levels_books launch reports the levels of the same slots (not of the
-whole pool) on the pool's processing stream.  The windows are
+Every tick advances ALL admitted episodes by one step.  Per capacity class,
+one call of the library's native tick executor (lob_serve_tick, which keeps
+the slots' progress) issues everything: the tick's upload (offsets, slots,
+restarts) from a pinned ring, one generator launch that writes the active
+slots' windows on the pool's generator stream, then one lob_process_batch
+launch that applies them and one lob_get_levels_books launch that reports the
+levels of the same slots on the pool's processing stream.  The windows are
 double-buffered, so the generator produces tick k+1 while tick k is being
 processed; the classes run on their own streams and overlap on the device.
+This module keeps admission and the episodes' bookkeeping.
 
 The host runs up to RING ticks ahead of the GPU (finishing times follow from
 the step counts, so no tick waits for the previous one).  The latency of an
@@ -48,6 +51,7 @@ import torch
 import lobgen
 
 from . import N_COUNTERS, Engine, lib
+from ._abi import LobServeDesc
 
 MSG_BYTES = 32
 RING = 8  # ticks the host may run ahead of the GPU
@@ -98,30 +102,15 @@ def footprint_bytes(capacity: int, trade_capacity: int, msgs_per_step: int) -> i
             + GEN_STATE_BYTES + MSG_BYTES * msgs_per_step)
 
 
-def _p(t, byte_off=0):
-    return ctypes.c_void_p(t.data_ptr() + byte_off)
-
-
-_cudart = None
-
-
-def _memcpy_h2d_async():
-    """cudaMemcpyAsync of the CUDA runtime torch loaded (raw pointers and
-    stream handle: a tick's upload without torch's stream bookkeeping)."""
-    global _cudart
-    if _cudart is None:
-        lib = ctypes.CDLL("libcudart.so.%d" % int(torch.version.cuda.split(".")[0]))
-        fn = lib.cudaMemcpyAsync
-        fn.restype = ctypes.c_int
-        fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
-                       ctypes.c_void_p]
-        _cudart = fn
-    return _cudart
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
 
 
 class _Pool:
     """Resident slots of one capacity class: an engine context over all slots,
-    per-slot generator state, double-buffered step windows, two streams."""
+    per-slot generator state, two window buffers, two streams, and the native
+    tick executor (lob_serve_*) that keeps the slots' progress and issues each
+    tick."""
 
     def __init__(self, capacity, slots, trade_capacity, depth, params, max_mps, collect):
         self.capacity, self.slots, self.depth, self.params = capacity, slots, depth, params
@@ -131,11 +120,6 @@ class _Pool:
         self.stream = torch.cuda.Stream(priority=-1)  # processing
         self.gstream = torch.cuda.Stream(priority=0)  # window generation
         S = slots
-        # packed per-tick upload (int64 words): offsets [S+1] | counts [S] |
-        # restart stream ids [S] | active slot ids (int32) [S] | restart slots (int32) [S]
-        self.o_cnt, self.o_sid, self.o_ids = S + 1, 2 * S + 1, 3 * S + 1
-        self.o_rid = self.o_ids + (S + 1) // 2
-        self.pack_words = self.o_rid + (S + 1) // 2
         with torch.cuda.stream(self.stream):
             self.engine = Engine(slots, capacity, trade_capacity, stream=self.stream)
             self.g_states = torch.zeros(S * lobgen.STATE_BYTES, dtype=torch.uint8, device="cuda")
@@ -145,8 +129,6 @@ class _Pool:
             self.geo_q = torch.from_numpy(lobgen.GEO_Q.view(np.int64)).cuda()
             self.win = [torch.empty((S * max_mps, 8), dtype=torch.int32, device="cuda")
                         for _ in range(2)]
-            self.d_pack = [torch.empty(self.pack_words, dtype=torch.int64, device="cuda")
-                           for _ in range(2)]
             self.levels = [torch.empty((S, depth), dtype=torch.int32, device="cuda")
                            for _ in range(4)]
             self.d_tcount = torch.empty(S, dtype=torch.int64, device="cuda")
@@ -154,132 +136,78 @@ class _Pool:
         self.reserved_bytes = (S * (book_bytes(capacity) + 8 + 32 * trade_capacity + 8
                                     + 8 * N_COUNTERS + GEN_STATE_BYTES)
                                + 2 * S * max_mps * MSG_BYTES)
-        # device addresses and handles used every tick (the buffers never move)
-        self.h_ps = ctypes.c_void_p(self.stream.cuda_stream)
-        self.h_gs = ctypes.c_void_p(self.gstream.cuda_stream)
-        self.a_win = [_p(w) for w in self.win]
-        self.a_pack = [dict(off=_p(d), cnt=_p(d, 8 * self.o_cnt), sid=_p(d, 8 * self.o_sid),
-                            ids=_p(d, 8 * self.o_ids), rid=_p(d, 8 * self.o_rid))
-                       for d in self.d_pack]
-        self.a_states, self.a_pools = _p(self.g_states), _p(self.g_pools)
-        self.a_geo_px, self.a_geo_q = _p(self.geo_px), _p(self.geo_q)
-        self.a_levels = [_p(x) for x in self.levels]
-        self.a_tcount = _p(self.d_tcount)
-        self.params_ref = ctypes.byref(self.params)
-        self.memcpy = _memcpy_h2d_async()
-        self.ev_gen = [torch.cuda.Event() for _ in range(2)]   # windows k ready
-        self.ev_used = [torch.cuda.Event() for _ in range(2)]  # windows k consumed
-        self.ring = []
-        for _ in range(RING):
-            pack = torch.empty(self.pack_words, dtype=torch.int64).pin_memory()
-            self.ring.append(dict(pack=pack, np=pack.numpy(), a_pack=_p(pack),
-                                  copied=torch.cuda.Event(),
-                                  g0=torch.cuda.Event(enable_timing=True),
-                                  g1=torch.cuda.Event(enable_timing=True),
-                                  t0=torch.cuda.Event(enable_timing=True),
-                                  t1=torch.cuda.Event(enable_timing=True),
-                                  busy=False, timed=False, n=0))
-        self.ring_pos = 0
-        self.tick = 0
+        lg = lobgen.cuda_lib()
+        addr = lambda f: ctypes.cast(f, ctypes.c_void_p).value  # noqa: E731
+        self.desc = LobServeDesc(
+            engine=self.engine.h.value, gen_params=ctypes.addressof(params),
+            gen_init=addr(lg.lobgen_dev_init_ids), gen_advance=addr(lg.lobgen_dev_advance),
+            d_geo_px=self.geo_px.data_ptr(), d_geo_q=self.geo_q.data_ptr(),
+            d_gen_states=self.g_states.data_ptr(), d_gen_pools=self.g_pools.data_ptr(),
+            d_win0=self.win[0].data_ptr(), d_win1=self.win[1].data_ptr(),
+            d_bid_px=self.levels[0].data_ptr(), d_bid_qty=self.levels[1].data_ptr(),
+            d_ask_px=self.levels[2].data_ptr(), d_ask_qty=self.levels[3].data_ptr(),
+            d_trade_counts=self.d_tcount.data_ptr(), proc_stream=self.stream.cuda_stream,
+            gen_stream=self.gstream.cuda_stream, slots=S, max_msgs=max_mps, depth=depth,
+            ring=RING)
+        lb = lib()
+        self.h = ctypes.c_void_p()
+        if lb.lob_serve_create(ctypes.byref(self.h), ctypes.byref(self.desc)) != 0:
+            raise RuntimeError("lob_serve_create: %s" % lb.lob_last_error().decode())
+        # the executor's outputs of a tick (host buffers reused every tick)
+        self.b_act = np.empty(S, np.int32)
+        self.b_fin = np.empty(S, np.int32)
+        self.b_n = np.zeros(2, np.int32)     # slots advanced, episodes finished
+        self.b_msgs = np.zeros(1, np.int64)
+        self._tick = lb.lob_serve_tick
+        self._tick_args = [None if not collect else ctypes.c_void_p(self.b_act.ctypes.data),
+                           ctypes.c_void_p(self.b_n.ctypes.data),
+                           ctypes.c_void_p(self.b_fin.ctypes.data),
+                           ctypes.c_void_p(self.b_n.ctypes.data + 4),
+                           ctypes.c_void_p(self.b_msgs.ctypes.data)]
         self.lat = []      # (GPU ms of a timed tick's processing, episodes in it)
         self.gen_ms = []   # GPU ms of a timed tick's window generation
-        self.free = list(range(slots - 1, -1, -1))
-        self.ep = np.full(slots, -1, np.int64)      # episode index in the slot, -1 free
-        self.step = np.zeros(slots, np.int64)
-        self.n_steps = np.zeros(slots, np.int64)
-        self.mps = np.zeros(slots, np.int64)
-        self.restart = []  # (slot, stream id) admitted since the last tick
+        self.ep = np.full(slots, -1, np.int64)  # episode index in the slot, -1 free
+        self.n_free = slots
         self.n_active = 0
         self.collect = collect
 
-    def _retire(self, st):
-        """Wait until a staging set's upload has landed; record its timings."""
-        st["copied"].synchronize()
-        if st["timed"]:
-            st["t1"].synchronize()
-            self.lat.append((st["t0"].elapsed_time(st["t1"]), st["n"]))
-            self.gen_ms.append(st["g0"].elapsed_time(st["g1"]))
-        st["busy"] = st["timed"] = False
-
     def flush(self):
-        for st in self.ring:
-            if st["busy"]:
-                self._retire(st)
+        """Wait for every tick issued; collect the timed ticks' times."""
+        lb = lib()
+        cnt = ctypes.c_int32()
+        if lb.lob_serve_timings(self.h, None, None, None, 0, ctypes.byref(cnt)) != 0:
+            raise RuntimeError("lob_serve_timings: %s" % lb.lob_last_error().decode())
+        n = cnt.value
+        if n:
+            pm, gm, k = np.empty(n, np.float32), np.empty(n, np.float32), np.empty(n, np.int32)
+            if lb.lob_serve_timings(self.h, pm.ctypes.data, gm.ctypes.data, k.ctypes.data, n,
+                                    ctypes.byref(cnt)) != 0:
+                raise RuntimeError("lob_serve_timings: %s" % lb.lob_last_error().decode())
+            self.lat.extend(zip(pm.tolist(), k.tolist()))
+            self.gen_ms.extend(gm.tolist())
 
     def admit(self, idx: int, ep: Episode):
         if ep.msgs_per_step > self.max_mps:
             raise ValueError("episode %d: %d messages per step above the pool's %d"
                              % (ep.id, ep.msgs_per_step, self.max_mps))
-        s = self.free.pop()
-        self.ep[s], self.step[s] = idx, 0
-        self.n_steps[s], self.mps[s] = ep.n_steps, ep.msgs_per_step
-        self.restart.append((s, ep.id))
+        slot = ctypes.c_int32()
+        if lib().lob_serve_admit(self.h, ep.id, ep.n_steps, ep.msgs_per_step,
+                                 ctypes.byref(slot)) != 0:
+            raise RuntimeError("lob_serve_admit: %s" % lib().lob_last_error().decode())
+        self.ep[slot.value] = idx
+        self.n_free -= 1
         self.n_active += 1
 
     def launch_step(self, timing=False):
-        """One step of every active slot, asynchronously: windows on the
-        generator stream, processing and levels on the processing stream.
-        Returns (active slots, messages)."""
-        act = np.flatnonzero(self.ep >= 0).astype(np.int32)
-        n = len(act)
-        cnt = self.mps[act]
-        st = self.ring[self.ring_pos]
-        self.ring_pos = (self.ring_pos + 1) % len(self.ring)
-        if st["busy"]:
-            self._retire(st)
-        buf = st["np"]
-        buf[0] = 0
-        np.cumsum(cnt, out=buf[1:n + 1])
-        buf[self.o_cnt:self.o_cnt + n] = cnt
-        nr = len(self.restart)
-        if nr:
-            rs = np.array(self.restart, dtype=np.int64)
-            buf[self.o_sid:self.o_sid + nr] = rs[:, 1]
-            buf[self.o_rid:].view(np.int32)[:nr] = rs[:, 0]
-        buf[self.o_ids:].view(np.int32)[:n] = act
-        self.restart = []
-        k = self.tick & 1
-        ap = self.a_pack[k]
-        lg = lobgen.cuda_lib()
-        lb = lib()
-        gs, ps = self.gstream, self.stream
-        # generator stream: the windows of this tick (buffer k is free once
-        # the processing of tick-2 has consumed it)
-        gs.wait_event(self.ev_used[k])
-        if self.memcpy(ap["off"], st["a_pack"], 8 * self.pack_words, 1, self.h_gs) != 0:
-            raise RuntimeError("cudaMemcpyAsync of the tick's upload failed")
-        st["copied"].record(gs)
-        st["busy"], st["timed"], st["n"] = True, timing, n
-        if timing:
-            st["g0"].record(gs)
-        if nr and lg.lobgen_dev_init_ids(self.params_ref, nr, ap["rid"], ap["sid"], self.a_states,
-                                         self.h_gs) != 0:
-            raise RuntimeError("lobgen_dev_init_ids failed")
-        if lg.lobgen_dev_advance(self.params_ref, self.a_geo_px, self.a_geo_q, n, ap["ids"],
-                                 self.a_states, self.a_pools, ap["cnt"], ap["off"], self.a_win[k],
-                                 self.h_gs) != 0:
-            raise RuntimeError("lobgen_dev_advance failed")
-        if timing:
-            st["g1"].record(gs)
-        self.ev_gen[k].record(gs)
-        # processing stream
-        ps.wait_event(self.ev_gen[k])
-        if timing:
-            st["t0"].record(ps)
-        h = self.engine.h
-        if nr and lb.lob_reset_books(h, ap["rid"], nr, self.h_ps) != 0:
-            raise RuntimeError("lob_reset_books failed")
-        if lb.lob_process_batch(h, self.a_win[k], ap["off"], ap["ids"], n, self.h_ps) != 0:
-            raise RuntimeError("lob_process_batch failed")
-        if lb.lob_get_levels_books(h, ap["ids"], n, self.depth, *self.a_levels, self.h_ps) != 0:
-            raise RuntimeError("lob_get_levels_books failed")
-        if self.collect:
-            lb.lob_get_trades(h, None, self.a_tcount, self.h_ps)
-        if timing:
-            st["t1"].record(ps)
-        self.ev_used[k].record(ps)
-        self.tick += 1
-        return act, int(cnt.sum())
+        """One step of every active slot, issued asynchronously by the native
+        executor (windows on the generator stream, processing and levels on
+        the processing stream).  Returns (active slots -- in collect mode
+        only --, messages, slots whose episode ended)."""
+        if self._tick(self.h, 1 if timing else 0, 1 if self.collect else 0, *self._tick_args) != 0:
+            raise RuntimeError("lob_serve_tick: %s" % lib().lob_last_error().decode())
+        n, nf = int(self.b_n[0]), int(self.b_n[1])
+        act = self.b_act[:n].copy() if self.collect else None
+        return act, int(self.b_msgs[0]), self.b_fin[:nf].copy()
 
     def capture_final(self):
         """The pool's books and counters as they stand once the work queued so
@@ -288,6 +216,17 @@ class _Pool:
             bk = self.engine.book()
             ctr, _ = self.engine.stats()
         return bk, ctr
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().lob_serve_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:
@@ -331,7 +270,7 @@ class Server:
             pool = self.pools.get(ep.capacity)
             if pool is None:
                 raise ValueError("no pool for capacity %d" % ep.capacity)
-            if pool.free and self.used + fps[i] <= self.budget:
+            if pool.n_free and self.used + fps[i] <= self.budget:
                 pool.admit(i, ep)
                 self.used += fps[i]
                 ep.admitted = now
@@ -383,11 +322,11 @@ class Server:
                 te = time.perf_counter()
                 launched = [(p, *p.launch_step(timing=True)) for p in busy]
             steps_done += active
-            msgs_done += sum(m for _, _, m in launched)
+            msgs_done += sum(m for _, _, m, _ in launched)
             now_after = (te - t0) if clock == "wall" else float(tick)
-            for p, act, _ in launched:
-                p.step[act] += 1
-                ended = act[p.step[act] >= p.n_steps[act]]
+            for p, _, _, ended in launched:
+                if not len(ended):
+                    continue
                 keep = [s for s in ended if self.keep_final or
                         episodes[int(p.ep[s])].id in self.capture_ids]
                 if keep:
@@ -399,7 +338,7 @@ class Server:
                     episodes[i].done = now_after
                     p.ep[s] = -1
                     p.n_active -= 1
-                    p.free.append(int(s))
+                    p.n_free += 1
                     self.used -= fps[i]
             tick += 1
             if max_ticks is not None and tick >= max_ticks:
@@ -443,7 +382,7 @@ class Server:
                 "queue": queue_len}
 
     def _record(self, episodes, launched):
-        for p, act, _ in launched:
+        for p, act, _, _ in launched:
             lv = [x.cpu().numpy() for x in p.levels]
             tc = p.d_tcount.cpu().numpy()
             for s in act:

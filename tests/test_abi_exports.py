@@ -60,3 +60,16 @@ def test_cpu_only_calls_fail_cleanly(lib):
     one = ctypes.c_void_p(16)
     assert lib.lob_get_levels_books(None, one, 1, 10, one, one, one, one, None) == -1
     assert b"lob_get_levels_books" in lib.lob_last_error()
+    # the serving executor checks its descriptor and handles before any CUDA call
+    lib.lob_serve_create.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert lib.lob_serve_create(ctypes.byref(out), None) == -1
+    from paper_2308_13289_b300._abi import LobServeDesc
+    desc = LobServeDesc(slots=4, max_msgs=10, depth=10, ring=8)  # null pointers
+    assert lib.lob_serve_create(ctypes.byref(out), ctypes.byref(desc)) == -1
+    assert b"invalid descriptor" in lib.lob_last_error() and not out.value
+    lib.lob_serve_tick.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32] + \
+        [ctypes.c_void_p] * 5
+    assert lib.lob_serve_tick(None, 0, 0, None, None, None, None, None) == -1
+    lib.lob_serve_destroy.argtypes = [ctypes.c_void_p]
+    assert lib.lob_serve_destroy(None) == 0
