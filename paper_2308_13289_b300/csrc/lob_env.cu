@@ -509,47 +509,83 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
 
 // Observation vector (Sec. 5.2.2) from one step's level-1 trace and the
 // environment state: one CTA per environment (grid-stride over environments),
-// thread k handles message k of the step.
+// thread k handles message k of the step.  The row (6M + 8 floats) is built in
+// shared memory and written with 16-byte stores when its size and the
+// output's alignment allow (M even, 16-byte aligned obs),
+// so the store pipe issues a quarter of the instructions of per-feature stores.
 __global__ void k_env_observe(const EnvStateDev* __restrict__ env, const Msg* __restrict__ replay,
                               int64_t stride_env, const int4* __restrict__ l1, int32_t M,
                               int32_t n_envs, int64_t passive_off, int32_t parent,
                               float* __restrict__ obs)
 {
+    extern __shared__ __align__(16) float srow[];
     const int64_t row = 6 * (int64_t)M + 8;
     const int64_t kSec = 1000000000;
     const int k = threadIdx.x;
+    const bool vec = (row & 3) == 0 && (reinterpret_cast<uintptr_t>(obs) & 15u) == 0;
+    // a best ask (1 .. INT32_MAX) plus an offset in 0 .. INT32_MAX stays below 2^32
+    const bool small_off = passive_off >= 0 && passive_off <= 0x7fffffffLL;
     for (int b = blockIdx.x; b < n_envs; b += gridDim.x) {
-        if (k >= M) continue;
-        const int4 r = l1[(int64_t)b * M + k];  // best bid price, its qty, best ask price, its qty
-        const bool hb = r.x > 0, ha = r.z > 0;
-        double mid = -1.0;
-        if (hb && ha)
-            mid = __ddiv_rn(__dadd_rn((double)r.x, (double)r.z), 2.0);
-        else if (hb)
-            mid = (double)r.x;
-        else if (ha)
-            mid = (double)r.z;
-        float* o = obs + (int64_t)b * row;
-        o[k] = __int2float_rn(r.x);
-        o[M + k] = __int2float_rn(r.z);
-        o[2 * M + k] = __double2float_rn(mid);
-        o[3 * M + k] = __ll2float_rn(ha ? (int64_t)r.z + passive_off : -1);
-        o[4 * M + k] = __ll2float_rn(hb && ha ? (int64_t)r.z - r.x : -1);
-        o[5 * M + 8 + k] = __ll2float_rn((int64_t)r.w - r.y);
-        if (k == M - 1) {
-            const EnvStateDev es = env[b];
-            const int64_t t_init = replay[(int64_t)b * stride_env].time_ns;
-            const int64_t tc = es.last_time, te = es.last_time - t_init;
-            float* sc = o + 5 * M;
-            sc[0] = __ll2float_rn(tc / kSec);
-            sc[1] = __ll2float_rn(tc % kSec);
-            sc[2] = __ll2float_rn(te / kSec);
-            sc[3] = __ll2float_rn(te % kSec);
-            sc[4] = __double2float_rn(es.p_init);
-            sc[5] = __double2float_rn(mid >= 0.0 ? __dsub_rn(mid, es.p_init) : 0.0);
-            sc[6] = __int2float_rn(parent);
-            sc[7] = __ll2float_rn(es.executed);
+        if (k < M) {
+            const int4 r = l1[(int64_t)b * M + k];  // best bid price, its qty, best ask price, its qty
+            const bool hb = r.x > 0, ha = r.z > 0;
+            // Every per-message feature in 32-bit arithmetic, with the bits of
+            // the binary64 definitions (the FP64 pipe of this GPU is narrow):
+            // the mid of two prices is RN(bid + ask) / 2 -- the sum is exact
+            // below 2^32 and halving commutes with rounding to float --, the
+            // spread and the quantity imbalance fit in int32 (both operands
+            // lie in 0 .. INT32_MAX), and the passive price fits in uint32
+            // whenever the offset does (decided once per launch).
+            float midf = -1.0f;
+            if (hb && ha)
+                midf = __uint2float_rn((uint32_t)r.x + (uint32_t)r.z) * 0.5f;
+            else if (hb)
+                midf = __int2float_rn(r.x);
+            else if (ha)
+                midf = __int2float_rn(r.z);
+            float passive = -1.0f;
+            if (ha) {
+                const int64_t pp = (int64_t)r.z + passive_off;
+                passive = small_off ? __uint2float_rn((uint32_t)pp) : __ll2float_rn(pp);
+            }
+            srow[k] = __int2float_rn(r.x);
+            srow[M + k] = __int2float_rn(r.z);
+            srow[2 * M + k] = midf;
+            srow[3 * M + k] = passive;
+            srow[4 * M + k] = hb && ha ? __int2float_rn(r.z - r.x) : -1.0f;
+            srow[5 * M + 8 + k] = __int2float_rn(r.w - r.y);
+            if (k == M - 1) {
+                double mid = -1.0;  // the last mid in binary64 for the drift feature
+                if (hb && ha)
+                    mid = __dmul_rn(__dadd_rn((double)r.x, (double)r.z), 0.5);
+                else if (hb)
+                    mid = (double)r.x;
+                else if (ha)
+                    mid = (double)r.z;
+                const EnvStateDev es = env[b];
+                const int64_t t_init = replay[(int64_t)b * stride_env].time_ns;
+                const int64_t tc = es.last_time, te = es.last_time - t_init;
+                float* sc = srow + 5 * M;
+                sc[0] = __ll2float_rn(tc / kSec);
+                sc[1] = __ll2float_rn(tc % kSec);
+                sc[2] = __ll2float_rn(te / kSec);
+                sc[3] = __ll2float_rn(te % kSec);
+                sc[4] = __double2float_rn(es.p_init);
+                sc[5] = __double2float_rn(mid >= 0.0 ? __dsub_rn(mid, es.p_init) : 0.0);
+                sc[6] = __int2float_rn(parent);
+                sc[7] = __ll2float_rn(es.executed);
+            }
         }
+        __syncthreads();
+        float* o = obs + (int64_t)b * row;
+        if (vec) {
+            const float4* src = reinterpret_cast<const float4*>(srow);
+            float4* dst = reinterpret_cast<float4*>(o);
+            for (int i = k; i < (int)(row >> 2); i += blockDim.x) dst[i] = src[i];
+        } else {
+            for (int i = k; i < (int)row; i += blockDim.x) o[i] = srow[i];
+        }
+        __syncthreads();
     }
 }
 
@@ -828,7 +864,8 @@ int lob_env_observe(lob_env* e, const lob_msg_t* d_replay, int64_t stride_env,
     const int M = e->cfg.msgs_per_step;
     const int threads = (M + 31) / 32 * 32;  // msgs_per_step <= 1024
     const int grid = c->cfg.n_books < c->num_sms * 16 ? c->cfg.n_books : c->num_sms * 16;
-    k_env_observe<<<grid, threads, 0, (cudaStream_t)stream>>>(
+    const size_t smem = (size_t)(6 * M + 8) * sizeof(float);  // at most 24.6 KB (M <= 1024)
+    k_env_observe<<<grid, threads, smem, (cudaStream_t)stream>>>(
         e->d_state, reinterpret_cast<const Msg*>(d_replay), stride_env,
         reinterpret_cast<const int4*>(d_l1), M, c->cfg.n_books,
         (int64_t)e->cfg.passive_ticks * e->cfg.tick_size, e->cfg.parent_qty, d_obs);
