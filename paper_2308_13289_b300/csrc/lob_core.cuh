@@ -545,8 +545,9 @@ __device__ __forceinline__ void add_order(Book& bk, int& n, int cap, int rule, i
     const int l = lane_id();
     SideVec<K> tmp;
     SideVec<K>& v = bk.template acquire<X>(tmp);
-    // the shift's cross-lane values do not depend on the insertion point:
-    // fetch them first so that their latency overlaps the search
+    // the shift's cross-lane values (the left neighbour's last slot) do not
+    // depend on where the new order goes: fetch them first, so that their
+    // latency overlaps the full-side test; the price also decides the place
     const int32_t pv_px = __shfl_up_sync(kFull, v.px[K - 1], 1);
     const int32_t pv_q = __shfl_up_sync(kFull, v.q[K - 1], 1);
     const int32_t pv_oid = __shfl_up_sync(kFull, v.oid[K - 1], 1);
@@ -1483,30 +1484,32 @@ __device__ __forceinline__ int4 level1_book(Book& bk, int n_bid, int n_ask)
             if (n_ask > 0) level1_scan<K>(bk.template side<1>(), n_ask, pa, qa);
         }
     } else {
-        // registers: every lane sums its slots at the best price, then one warp
-        // reduction per side (32-bit while no lane's part can overflow it)
+        // registers: every lane sums its slots at the best price, saturated at
+        // INT32_MAX (a saturated part means a saturated total), then the 16-bit
+        // halves of the parts are summed over the warp: both sums are exact in
+        // 32 bits (below 2^21), and the total saturates at INT32_MAX
         const int l = lane_id();
         SideVec<K> tmp;
         SideVec<K>& vb = bk.template acquire<0>(tmp);
         SideVec<K>& va = bk.template acquire<1>(tmp);
         const int32_t bb = bk.template best_px<0>(n_bid);
         const int32_t ba = bk.template best_px<1>(n_ask);
-        int64_t lb = 0, la = 0;
+        uint32_t sb = 0, sa = 0;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            lb += (l * K + j < n_bid && vb.px[j] == bb) ? vb.q[j] : 0;
-            la += (l * K + j < n_ask && va.px[j] == ba) ? va.q[j] : 0;
+            sb = sat_add(sb, (l * K + j < n_bid && vb.px[j] == bb) ? (uint32_t)vb.q[j] : 0u);
+            sa = sat_add(sa, (l * K + j < n_ask && va.px[j] == ba) ? (uint32_t)va.q[j] : 0u);
         }
-        // a lane's part is below 2^33 (K <= 4 quantities < 2^31): its 16-bit
-        // low and high halves sum over 32 lanes without overflow, exactly
-        const unsigned b_lo = __reduce_add_sync(kFull, (unsigned)(lb & 0xffff));
-        const unsigned b_hi = __reduce_add_sync(kFull, (unsigned)(lb >> 16));
-        const unsigned a_lo = __reduce_add_sync(kFull, (unsigned)(la & 0xffff));
-        const unsigned a_hi = __reduce_add_sync(kFull, (unsigned)(la >> 16));
-        qb = ((int64_t)b_hi << 16) + b_lo;
-        qa = ((int64_t)a_hi << 16) + a_lo;
+        const uint32_t b_lo = __reduce_add_sync(kFull, sb & 0xffffu);
+        const uint32_t b_hi = __reduce_add_sync(kFull, sb >> 16);
+        const uint32_t a_lo = __reduce_add_sync(kFull, sa & 0xffffu);
+        const uint32_t a_hi = __reduce_add_sync(kFull, sa >> 16);
+        // hi >= 2^15 means a total of at least 2^31; below, (hi << 16) + lo < 2^32
+        const uint32_t tb = b_hi >= 0x8000u ? (uint32_t)kMaxInt : min((b_hi << 16) + b_lo, (uint32_t)kMaxInt);
+        const uint32_t ta = a_hi >= 0x8000u ? (uint32_t)kMaxInt : min((a_hi << 16) + a_lo, (uint32_t)kMaxInt);
         pb = n_bid > 0 ? bb : -1;
         pa = n_ask > 0 ? ba : -1;
+        return make_int4(pb, (int32_t)tb, pa, (int32_t)ta);
     }
     return make_int4(pb, (int32_t)min(qb, (int64_t)kMaxInt), pa,
                      (int32_t)min(qa, (int64_t)kMaxInt));
