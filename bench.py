@@ -672,7 +672,13 @@ def run_uneven(args, rank):
             if i >= args.warmup:
                 times.append(a.elapsed_time(b))
         ms = float(np.mean(times))
-        res[order] = {"ms_per_step": round(ms, 4), "msgs_per_s": round(res["messages"] / ms * 1e3, 1)}
+        trades = int(e.stats()[0][:, 6].sum().item())
+        # messages, trades, book state in and out, offsets and book ids
+        alg = 32 * res["messages"] + 32 * trades + 2 * n * eng_book_bytes(w["capacity"]) + \
+            8 * (n + 1) + 4 * n
+        peak, _ = measured_peaks()
+        res[order] = {"ms_per_step": round(ms, 4), "msgs_per_s": round(res["messages"] / ms * 1e3, 1),
+                      "algorithmic_bytes": alg, "hbm_frac": round(alg / (ms / 1e3) / 1e9 / peak, 5)}
         if order == "longest_first" and rank == 0:
             # every book against the oracle replaying its own stream
             ok, secs = replay_oracle_check(e, params, ids, counts, w["capacity"], tcap)
@@ -830,6 +836,7 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
     res["graph_equals_per_step"] = all(torch.equal(x, y) for x, y in zip(ref, snapshot()))
     del g
     std_out = {k: v.cpu().numpy() for k, v in out.items()}  # the stand-in agent's episode
+    std_trades = int(e.stats()[0][:, 6].sum().item())
     st_, p0_ = env.state()
     std_final = dict(state=st_.cpu().numpy(), p_init=p0_.cpu().numpy(),
                      books={k: v.cpu().numpy() for k, v in e.book().items()})
@@ -869,12 +876,28 @@ def run_rl(args, rank, name="rl_exec_8192x400"):
                 times.append(a.elapsed_time(b))
         forms[name] = float(np.mean(times))
     del g
+    policy_trades = int(e.stats()[0][:, 6].sum().item())
+    # algorithmic bytes of an episode (what each form must move): the data
+    # messages, the trades, the per-step outputs (levels, reward, fills), the
+    # agent's input (draws; or actions, then the trace and the observation,
+    # the trace read back by it), and the books' state in and out once per
+    # launch
+    depth = env.depth
+    state = 2 * n * eng_book_bytes(w["capacity"])
+    std_alg = n * steps * (per * 32 + 4 * depth * 4 + 4 + 16 + 4) + 32 * std_trades
+    pol_alg = n * steps * (per * 32 + 4 * depth * 4 + 4 + 16 + 16 + 2 * 16 * per +
+                           (6 * per + 8) * 4) + 32 * policy_trades + steps * state
+    peak, _ = measured_peaks()
     for name, ms in forms.items():
+        alg = pol_alg if name.startswith("policy") else \
+            std_alg + (state if name == "persistent_episode" else steps * state)
         res[name] = {"ms_per_episode": round(ms, 3),
                      "env_steps_per_s": round(n * steps / ms * 1e3, 1),
                      "data_msgs_per_s": round(n * steps * per / ms * 1e3, 1),
                      "launches": (1 if name == "persistent_episode" else
-                                  2 * steps if name.startswith("policy") else steps)}
+                                  2 * steps if name.startswith("policy") else steps),
+                     "algorithmic_bytes": alg,
+                     "hbm_frac": round(alg / (ms / 1e3) / 1e9 / peak, 5)}
     if rank == 0:
         # every environment, every step, against the oracle's environments
         hd = lobgen.agent_draws(w["seed"] + 1, n, steps)
