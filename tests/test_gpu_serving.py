@@ -155,3 +155,31 @@ def test_admission_respects_hbm_budget():
     assert rep["max_hbm_bytes_admitted"] == 5 * fp
     assert rep["max_queue"] > 0
     assert rep["episode_steps"] == sum(e.n_steps for e in eps)
+
+
+def test_degenerate_episodes_empty_windows_single_steps_and_slot_reuse():
+    """Episodes with empty step windows (0 messages a step), single-step
+    episodes and one slot per class, so every slot is reused many times on the
+    run-ahead path: every episode's final book and counters equal the oracle
+    replaying it (an empty window leaves the book as it was)."""
+    from paper_2308_13289_b300.serve import Episode, Server
+    rng = np.random.default_rng(21)
+    eps = []
+    for i in range(30):
+        kind = i % 3
+        eps.append(Episode(id=5000 + i, capacity=int(rng.choice((7, 250))),
+                           n_steps=1 if kind == 0 else int(rng.integers(2, 9)),
+                           msgs_per_step=0 if kind == 1 else int(rng.integers(20, 61)),
+                           arrival=float(i // 4)))
+    srv = Server(capacities=(7, 250), trade_capacity=512, max_slots=1, keep_final=True,
+                 seed=SEED, msgs_per_step=(0, 60))
+    rep = srv.run(_clone(eps), clock="virtual")
+    assert rep["episode_steps"] == sum(e.n_steps for e in eps)
+    assert set(srv.final_books) == {e.id for e in eps}
+    for ep in eps:
+        _, book, ctr = _oracle_episode(ep)
+        for k, v in book.items():
+            assert np.array_equal(v, srv.final_books[ep.id][k]), (ep.id, k)
+        assert np.array_equal(srv.final_counters[ep.id], ctr), ep.id
+        if ep.msgs_per_step == 0:
+            assert int(srv.final_books[ep.id]["count"].sum()) == 0
