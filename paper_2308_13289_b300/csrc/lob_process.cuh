@@ -37,10 +37,15 @@ struct ProcArgs {
     int32_t* l1;  // level-1 trace [message][4], or null
 };
 
+// Each of the two chunk buffers holds one message more than a chunk, so the
+// message loop can always load the next message (the one past a chunk's end
+// is read and never used) without a bounds test.
+__host__ __device__ constexpr int chunk_stride(int chunk) { return (chunk + 1) * 32; }
+
 template <int K>
 __host__ __device__ constexpr int warp_smem_bytes(int chunk)
 {
-    return ((Geo<K>::BOOK_BYTES + 2 * chunk * 32 + 16) + 127) / 128 * 128;
+    return ((Geo<K>::BOOK_BYTES + 2 * chunk_stride(chunk) + 16) + 127) / 128 * 128;
 }
 
 // threads per CTA the processing kernel is compiled for (bounds registers)
@@ -62,7 +67,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
     char* base = smem + warp * warp_smem_bytes<K>(chunk);
     char* image = base;  // staged book image (the whole book for the shared-memory policy)
     char* msgbuf = base + Geo<K>::BOOK_BYTES;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk * 32);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk_stride(chunk));
     const int total_warps = gridDim.x * W;
 
     if (l == 0) {
@@ -109,7 +114,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                 const uint32_t cnt = (uint32_t)min((int64_t)chunk, hi - c0);
                 mbar_expect_tx(&bar[st], cnt * 32 + (c == 0 ? Geo<K>::BOOK_BYTES : 0));
                 if (c == 0) bulk_g2s(image, gbook, Geo<K>::BOOK_BYTES, &bar[st]);
-                bulk_g2s(msgbuf + st * chunk * 32, a.msgs + c0, cnt * 32, &bar[st]);
+                bulk_g2s(msgbuf + st * chunk_stride(chunk), a.msgs + c0, cnt * 32, &bar[st]);
             }
         }
         int n_bid = a.counts[2 * b], n_ask = a.counts[2 * b + 1];
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                 break;
             }
             if (c == 0) bk.from_image(image);
-            int4* mb = reinterpret_cast<int4*>(msgbuf + st * chunk * 32);
+            int4* mb = reinterpret_cast<int4*>(msgbuf + st * chunk_stride(chunk));
             const int cnt = (int)min((int64_t)chunk, hi - (lo + (int64_t)c * chunk));
             // pre-pass, 32 messages at a time: validate and classify (the part of
             // Sec. 4.2 that does not depend on the book); the dispatch code
@@ -157,10 +162,8 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
             int4 na = mb[0], nb = mb[1];
             for (int i = 0; i < cnt; ++i) {
                 const int4 ha = na, hb = nb;
-                if (i + 1 < cnt) {
-                    na = mb[2 * i + 2];
-                    nb = mb[2 * i + 3];
-                }
+                na = mb[2 * i + 2];  // past the chunk's end: the padding message, unused
+                nb = mb[2 * i + 3];
                 apply_message<K, false>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x, hb.y,
                                  hb.z, hb.w, ts, tally, obs, kSnap);
                 check_book<K>(bk, n_bid, n_ask, a.cap, a.status);
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(max_threads<K>(), 1) k_process(ProcArgs a)
                 const int64_t c0 = lo + (int64_t)(c + 2) * chunk;
                 const uint32_t cn = (uint32_t)min((int64_t)chunk, hi - c0);
                 mbar_expect_tx(&bar[st], cn * 32);
-                bulk_g2s(msgbuf + st * chunk * 32, a.msgs + c0, cn * 32, &bar[st]);
+                bulk_g2s(msgbuf + st * chunk_stride(chunk), a.msgs + c0, cn * 32, &bar[st]);
             }
         }
         if (failed) break;
