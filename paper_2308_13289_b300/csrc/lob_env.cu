@@ -92,11 +92,16 @@ __device__ __forceinline__ void fence_proxy_async_global()
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+// Each of the two step buffers holds one message more than a step, and the
+// agent buffer more than a step's agent orders, so the message loop always
+// loads the next message (past the end: padding, never used) without a test.
+__host__ __device__ constexpr int env_stage_stride(int chunk) { return (chunk + 1) * 32; }
+
 template <int K>
 __host__ __device__ constexpr int env_warp_smem(int chunk)
 {
-    return ((Geo<K>::BOOK_BYTES + 2 * chunk * 32 + 16 + kLevelScratch + kAgentRecs * 32) + 127) /
-           128 * 128;
+    return ((Geo<K>::BOOK_BYTES + 2 * env_stage_stride(chunk) + 16 + kLevelScratch +
+             kAgentRecs * 32) + 127) / 128 * 128;
 }
 
 // kTrace: the kernel also writes the level-1 state after every data message;
@@ -129,8 +134,9 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
     char* base = smem + warp * env_warp_smem<K>(chunk);
     char* image = base;
     char* msgbuf = base + Geo<K>::BOOK_BYTES;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * chunk * 32);
-    unsigned long long* lq = reinterpret_cast<unsigned long long*>(msgbuf + 2 * chunk * 32 + 16);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(msgbuf + 2 * env_stage_stride(chunk));
+    unsigned long long* lq =
+        reinterpret_cast<unsigned long long*>(msgbuf + 2 * env_stage_stride(chunk) + 16);
     int32_t* lp = reinterpret_cast<int32_t*>(lq + 128);
     int4* agent_buf = reinterpret_cast<int4*>(lp + 64);
     const int total_warps = gridDim.x * W;
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
                 const uint32_t st = (g + c) & 1;
                 mbar_expect_tx(&bar[st], bytes + (c == 0 ? Geo<K>::BOOK_BYTES : 0));
                 if (c == 0) bulk_g2s(image, gbook, Geo<K>::BOOK_BYTES, &bar[st]);
-                bulk_g2s(msgbuf + st * chunk * 32,
+                bulk_g2s(msgbuf + st * env_stage_stride(chunk),
                          my + (int64_t)(a.step0 + r0 + c) * a.msgs_per_step, bytes, &bar[st]);
             }
         }
@@ -229,7 +235,7 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
                 break;
             }
             if (rr == 0) bk.from_image(image);
-            int4* mb = reinterpret_cast<int4*>(msgbuf + st * chunk * 32);
+            int4* mb = reinterpret_cast<int4*>(msgbuf + st * env_stage_stride(chunk));
             const int cnt = a.msgs_per_step;
             for (int i = l; i < cnt; i += 32) {
                 const int4 h = mb[2 * i];
@@ -387,10 +393,8 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
                 int4 na = src[0], nb = src[1];
                 for (int i = 0; i < count; ++i) {
                     const int4 ha = na, hb = nb;
-                    if (i + 1 < count) {
-                        na = src[2 * i + 2];
-                        nb = src[2 * i + 3];
-                    }
+                    na = src[2 * i + 2];  // past the end: padding, unused
+                    nb = src[2 * i + 3];
                     apply_message<K, true>(bk, n_bid, n_ask, a.cap, a.rule, ha.x, ha.z, ha.w, hb.x,
                                      hb.y, hb.z, hb.w, ts, tally, obs, kSnap);
                     check_book<K>(bk, n_bid, n_ask, a.cap, a.status);
@@ -438,7 +442,7 @@ __global__ void __launch_bounds__(K >= 8 ? 256 : 128, K >= 8 ? 1 : 3) k_env(EnvA
             if (r + 2 < r1 && l == 0) {
                 fence_proxy_async();
                 mbar_expect_tx(&bar[st], bytes);
-                bulk_g2s(msgbuf + st * chunk * 32, my + (int64_t)(t + 2) * a.msgs_per_step, bytes,
+                bulk_g2s(msgbuf + st * env_stage_stride(chunk), my + (int64_t)(t + 2) * a.msgs_per_step, bytes,
                          &bar[st]);
             }
         }
