@@ -952,9 +952,16 @@ def run_serving(args, rank):
             sample.append(min(mine, key=size))
     if eps:
         sample.append(max(eps, key=size))
-    for leg, budget in (("uncontended", 2 << 30), ("contended", args.serving_budget_mib << 20)):
+    # the third leg splits every capacity class at 300 messages per step: a
+    # pool's tick lasts as long as its longest window, so short windows get
+    # their own pools (latency against throughput: more pools, more host work
+    # per tick)
+    for leg, budget, buckets in (("uncontended", 2 << 30, ()),
+                                 ("contended", args.serving_budget_mib << 20, ()),
+                                 ("bucketed", 2 << 30, (300,))):
         srv = Server(capacities=w["capacities"], seed=w["seed"], hbm_budget=budget,
-                     msgs_per_step=w["msgs_per_step"], capture_ids=[e.id for e in sample])
+                     msgs_per_step=w["msgs_per_step"], capture_ids=[e.id for e in sample],
+                     window_buckets=buckets)
         rep = srv.run([copy.copy(e) for e in eps], clock="wall")
         if rank == 0:
             rep["parity"] = serving_parity(srv, sample, w["seed"])

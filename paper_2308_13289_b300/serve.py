@@ -230,11 +230,15 @@ class _Pool:
 
 
 class Server:
-    """Continuous batching over per-capacity slot pools with HBM admission."""
+    """Continuous batching over slot pools with HBM admission: one pool per
+    capacity, or, with window_buckets (ascending message counts), one per
+    capacity and range of messages per step -- a pool's tick lasts as long
+    as its longest window, so episodes with short windows finish their steps
+    sooner in a pool of their own."""
 
     def __init__(self, capacities=(100, 250, 500), hbm_budget=2 << 30, trade_capacity=2048,
                  depth=10, seed=20230829, max_slots=4096, collect=False, keep_final=False,
-                 msgs_per_step=(100, 500), capture_ids=None):
+                 msgs_per_step=(100, 500), capture_ids=None, window_buckets=()):
         self.params = lobgen.make_params(seed, "pm1")
         self.depth = depth
         self.budget = hbm_budget
@@ -243,11 +247,18 @@ class Server:
         self.keep_final = keep_final or collect
         self.capture_ids = set(capture_ids) if capture_ids else set()
         lo, hi = msgs_per_step
+        # message-count ranges of the pools of one capacity: (lo, b0], (b0, b1], ..., (bk, hi]
+        self.bounds = [b for b in sorted(window_buckets) if lo <= b < hi]
+        edges = [lo - 1] + self.bounds + [hi]
         self.pools = {}
         for c in capacities:
-            # as many slots as the budget holds of the smallest episodes
-            slots = int(min(max_slots, max(1, hbm_budget // footprint_bytes(c, trade_capacity, lo))))
-            self.pools[c] = _Pool(c, slots, trade_capacity, depth, self.params, hi, collect)
+            for k in range(len(edges) - 1):
+                w_lo, w_hi = edges[k] + 1, edges[k + 1]
+                # as many slots as the budget holds of the smallest episodes
+                slots = int(min(max_slots, max(1, hbm_budget //
+                                               footprint_bytes(c, trade_capacity, max(w_lo, 0)))))
+                self.pools[(c, k)] = _Pool(c, slots, trade_capacity, depth, self.params, w_hi,
+                                           collect)
         self.used = 0
         self.records = collections.defaultdict(list)  # episode id -> per-step outputs
         self.final_books = {}
@@ -255,6 +266,10 @@ class Server:
 
     def footprint(self, ep):
         return footprint_bytes(ep.capacity, self.tcap, ep.msgs_per_step)
+
+    def pool_of(self, ep):
+        k = sum(1 for b in self.bounds if ep.msgs_per_step > b)
+        return self.pools.get((ep.capacity, k))
 
     def _admit_waiting(self, episodes, waiting, fps, min_fp, now):
         """First fit in arrival order; stops as soon as no waiting episode
@@ -267,7 +282,7 @@ class Server:
                 break
             i = waiting.popleft()
             ep = episodes[i]
-            pool = self.pools.get(ep.capacity)
+            pool = self.pool_of(ep)
             if pool is None:
                 raise ValueError("no pool for capacity %d" % ep.capacity)
             if pool.n_free and self.used + fps[i] <= self.budget:
@@ -347,13 +362,17 @@ class Server:
         wall = time.perf_counter() - t0
         gen_ms = []
         per_pool = {}
-        for c, p in self.pools.items():
+        by_cap = collections.defaultdict(list)
+        for (c, _), p in self.pools.items():
             p.flush()
-            if p.lat:
-                pl = np.repeat(np.asarray([ms for ms, _ in p.lat]), [n for _, n in p.lat])
+            by_cap[c] += p.lat
+        for c, pl in by_cap.items():
+            if pl:
+                pl = np.repeat(np.asarray([ms for ms, _ in pl]), [n for _, n in pl])
                 per_pool[c] = {"p50_step_ms": float(np.percentile(pl, 50)),
                                "p99_step_ms": float(np.percentile(pl, 99)),
                                "episode_steps": int(len(pl))}
+        for p in self.pools.values():
             for ms, n in p.lat:
                 lat.append(ms / 1e3)
                 weights.append(n)
@@ -377,7 +396,9 @@ class Server:
                 "max_active": max_active, "max_hbm_bytes_admitted": max_used,
                 "hbm_budget_bytes": self.budget,
                 "hbm_reserved_bytes": sum(p.reserved_bytes for p in self.pools.values()),
-                "slots": {c: p.slots for c, p in self.pools.items()},
+                "slots": {("%d" % c if not self.bounds else "%d/%d" % (c, k)): p.slots
+                          for (c, k), p in self.pools.items()},
+                "window_buckets": list(self.bounds),
                 "per_capacity": per_pool,
                 "queue": queue_len}
 

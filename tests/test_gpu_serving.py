@@ -183,3 +183,32 @@ def test_degenerate_episodes_empty_windows_single_steps_and_slot_reuse():
         assert np.array_equal(srv.final_counters[ep.id], ctr), ep.id
         if ep.msgs_per_step == 0:
             assert int(srv.final_books[ep.id]["count"].sum()) == 0
+
+
+def test_window_buckets_route_episodes_and_keep_results():
+    """Pools split by messages per step (window_buckets): every episode runs in
+    the pool of its capacity and window range, and its final book and
+    counters equal the oracle's and the unsplit server's."""
+    from paper_2308_13289_b300.serve import Server
+    eps = _mix(36, seed=13)
+    runs = {}
+    for buckets in ((), (30, 45)):
+        srv = Server(capacities=CAPS, trade_capacity=512, max_slots=4, keep_final=True,
+                     seed=SEED, msgs_per_step=(20, 60), window_buckets=buckets)
+        rep = srv.run(_clone(eps), clock="virtual")
+        assert rep["episode_steps"] == sum(e.n_steps for e in eps)
+        assert len(srv.pools) == len(CAPS) * (len(buckets) + 1)
+        for ep in eps:
+            p = srv.pool_of(ep)
+            assert p.capacity == ep.capacity and ep.msgs_per_step <= p.max_mps
+        runs[buckets] = srv
+    a, b = runs[()], runs[(30, 45)]
+    for ep in eps:
+        for k, v in a.final_books[ep.id].items():
+            assert np.array_equal(v, b.final_books[ep.id][k]), (ep.id, k)
+        assert np.array_equal(a.final_counters[ep.id], b.final_counters[ep.id]), ep.id
+    for ep in eps[::5]:
+        _, book, ctr = _oracle_episode(ep)
+        for k, v in book.items():
+            assert np.array_equal(v, b.final_books[ep.id][k]), (ep.id, k)
+        assert np.array_equal(b.final_counters[ep.id], ctr), ep.id
