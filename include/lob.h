@@ -237,8 +237,9 @@ int lob_get_levels(lob_ctx* ctx, int32_t depth, int32_t* d_bid_px, int32_t* d_bi
 
 /* The same levels for the books listed in d_book_ids (int32[n_active],
  * device, caller-owned; e.g. the ids just passed to lob_process_batch), each
- * written to its own row of the int32[n_books][depth] outputs; the rows of
- * books not listed are left as they are.  An id outside 0..n_books-1 sets
+ * written to its own row of the int32[n_books][depth] outputs (a book listed
+ * twice is written twice with the same values); the rows of books not listed
+ * are left as they are.  An id outside 0..n_books-1 sets
  * LOB_STATUS_BAD_BOOK and is skipped.  n_active 0 launches nothing (then
  * d_book_ids may be NULL; otherwise NULL is LOB_E_INVAL).  This is
  * the per-step level output of a batch in which only some books advanced (a
