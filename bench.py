@@ -440,7 +440,9 @@ def run_engine(args):
                            "trades_per_step_per_gpu": trades_per_step,
                            "trade_capacity": tcap, "form": "persistent", "launch": launch,
                            "l2": "inputs larger than L2 (%.2f GB of messages)" % (total_msgs * 32 / 1e9),
-                           "seed": w["seed"]},
+                           "seed": w["seed"],
+                           # independent books: every rank runs its own, no data-path collective
+                           "parallelism": "book-sharded x%d" % world},
                 "plain": plain, "plain_graph": plain_graph,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "parity": parity,
