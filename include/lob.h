@@ -9,11 +9,15 @@
  * Conventions for every entry point below:
  *   - Pointers named d_* are DEVICE pointers owned by the caller (for example
  *     torch CUDA tensors); the library never frees them and keeps no reference
- *     to them after the call returns.  The library owns only what lob_create /
- *     lob_env_create allocate (book state, trade log, counters, work queue).
+ *     to them after the call returns (the serving executor keeps the buffers
+ *     of its descriptor until lob_serve_destroy).  The library owns only what
+ *     lob_create / lob_env_create / lob_serve_create allocate (book state,
+ *     trade log, counters, work queue; the executor's upload buffers, pinned
+ *     ring and events).
  *   - Every call is asynchronous and ordered on `stream` (a cudaStream_t; NULL
  *     means the legacy default stream).  Results are ready once the stream has
- *     reached the call.
+ *     reached the call.  The serving executor issues on the two streams of its
+ *     descriptor and waits on the host only where its calls say so.
  *   - Return value: LOB_OK (0) or a negative LOB_E_* code; nothing is thrown
  *     across the ABI.  Argument errors are detected on the host before any
  *     launch and leave the context untouched.  lob_last_error() describes the
