@@ -551,6 +551,11 @@ int lob_serve_tick(lob_serve* s, int32_t timing, int32_t collect, int32_t* h_act
                    int32_t* n_active, int32_t* h_finished, int32_t* n_finished,
                    int64_t* n_msgs);
 
+/* 1 when a tick issued now would not wait on the host (the ring buffer it
+ * would reuse is free), 0 when it would; never waits.  LOB_E_INVAL for NULL,
+ * LOB_E_CUDA when a recorded tick failed. */
+int lob_serve_ready(lob_serve* s);
+
 /* Waits for every tick issued so far; *count = timed ticks recorded.  When cap
  * >= *count, copies, oldest first, each tick's processing time (ms, from its
  * windows being ready to its levels written, on proc_stream), generation time

@@ -69,6 +69,7 @@ SIGNATURES = {
     "lob_serve_admit": (ctypes.c_int, [vp, ctypes.c_uint64, i64, i32, ctypes.POINTER(i32)]),
     "lob_serve_tick": (ctypes.c_int, [vp, i32, i32, vp, vp, vp, vp, vp]),
     "lob_serve_timings": (ctypes.c_int, [vp, vp, vp, vp, i32, ctypes.POINTER(i32)]),
+    "lob_serve_ready": (ctypes.c_int, [vp]),
     "lob_serve_destroy": (ctypes.c_int, [vp]),
     "lob_last_error": (ctypes.c_char_p, []),
     "lob_abi_version": (ctypes.c_int, []),

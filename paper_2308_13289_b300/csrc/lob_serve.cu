@@ -294,6 +294,22 @@ int lob_serve_tick(lob_serve* s, int32_t timing, int32_t collect, int32_t* h_act
     return LOB_OK;
 }
 
+int lob_serve_ready(lob_serve* s)
+{
+    if (!s) {
+        lob_set_error("lob_serve_ready: null executor");
+        return LOB_E_INVAL;
+    }
+    const lob_serve::Entry& e = s->ring[s->pos];
+    if (!e.busy) return 1;
+    for (cudaEvent_t ev : {e.copied, e.timed ? e.t1 : e.copied}) {
+        const cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaErrorNotReady) return 0;
+        if (q != cudaSuccess) return lob_cuda_fail(q, "lob_serve_ready");
+    }
+    return 1;
+}
+
 int lob_serve_timings(lob_serve* s, float* proc_ms, float* gen_ms, int32_t* n_in_tick,
                       int32_t cap, int32_t* count)
 {

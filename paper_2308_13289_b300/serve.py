@@ -202,12 +202,19 @@ class _Pool:
         """One step of every active slot, issued asynchronously by the native
         executor (windows on the generator stream, processing and levels on
         the processing stream).  Returns (active slots -- in collect mode
-        only --, messages, slots whose episode ended)."""
+        only --, messages, slots whose episode ended, episodes advanced)."""
         if self._tick(self.h, 1 if timing else 0, 1 if self.collect else 0, *self._tick_args) != 0:
             raise RuntimeError("lob_serve_tick: %s" % lib().lob_last_error().decode())
         n, nf = int(self.b_n[0]), int(self.b_n[1])
         act = self.b_act[:n].copy() if self.collect else None
-        return act, int(self.b_msgs[0]), self.b_fin[:nf].copy()
+        return act, int(self.b_msgs[0]), self.b_fin[:nf].copy(), n
+
+    def ready(self):
+        """Whether a tick issued now would not wait for the GPU."""
+        r = lib().lob_serve_ready(self.h)
+        if r < 0:
+            raise RuntimeError("lob_serve_ready: %s" % lib().lob_last_error().decode())
+        return r == 1
 
     def capture_final(self):
         """The pool's books and counters as they stand once the work queued so
@@ -238,7 +245,8 @@ class Server:
 
     def __init__(self, capacities=(100, 250, 500), hbm_budget=2 << 30, trade_capacity=2048,
                  depth=10, seed=20230829, max_slots=4096, collect=False, keep_final=False,
-                 msgs_per_step=(100, 500), capture_ids=None, window_buckets=()):
+                 msgs_per_step=(100, 500), capture_ids=None, window_buckets=(),
+                 independent=False):
         self.params = lobgen.make_params(seed, "pm1")
         self.depth = depth
         self.budget = hbm_budget
@@ -246,6 +254,10 @@ class Server:
         self.collect = collect
         self.keep_final = keep_final or collect
         self.capture_ids = set(capture_ids) if capture_ids else set()
+        # independent=True: a loop pass issues a tick only to the pools whose
+        # tick would not wait for the GPU, so pools of short windows advance
+        # at their own pace instead of the slowest pool's (run-ahead path only)
+        self.independent = independent
         lo, hi = msgs_per_step
         # message-count ranges of the pools of one capacity: (lo, b0], (b0, b1], ..., (bk, hi]
         self.bounds = [b for b in sorted(window_buckets) if lo <= b < hi]
@@ -335,11 +347,16 @@ class Server:
                 self._record(episodes, launched)
             else:
                 te = time.perf_counter()
+                if self.independent:
+                    busy = [p for p in busy if p.ready()]
+                    if not busy:  # every pool's next tick would wait: let the GPU catch up
+                        time.sleep(0)
+                        continue
                 launched = [(p, *p.launch_step(timing=True)) for p in busy]
-            steps_done += active
-            msgs_done += sum(m for _, _, m, _ in launched)
+            steps_done += sum(n for *_, n in launched)
+            msgs_done += sum(m for _, _, m, _, _ in launched)
             now_after = (te - t0) if clock == "wall" else float(tick)
-            for p, _, _, ended in launched:
+            for p, _, _, ended, _ in launched:
                 if not len(ended):
                     continue
                 keep = [s for s in ended if self.keep_final or
@@ -403,7 +420,7 @@ class Server:
                 "queue": queue_len}
 
     def _record(self, episodes, launched):
-        for p, act, _, _ in launched:
+        for p, act, _, _, _ in launched:
             lv = [x.cpu().numpy() for x in p.levels]
             tc = p.d_tcount.cpu().numpy()
             for s in act:

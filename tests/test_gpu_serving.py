@@ -186,15 +186,18 @@ def test_degenerate_episodes_empty_windows_single_steps_and_slot_reuse():
 
 
 def test_window_buckets_route_episodes_and_keep_results():
-    """Pools split by messages per step (window_buckets): every episode runs in
-    the pool of its capacity and window range, and its final book and
-    counters equal the oracle's and the unsplit server's."""
+    """Pools split by messages per step (window_buckets), each ticking at its
+    own pace: every episode runs in the pool of its capacity and window
+    range, and its final book and counters equal the oracle's and the
+    unsplit lockstep server's."""
     from paper_2308_13289_b300.serve import Server
     eps = _mix(36, seed=13)
     runs = {}
     for buckets in ((), (30, 45)):
+        # the split pools tick at their own pace (independent scheduling)
         srv = Server(capacities=CAPS, trade_capacity=512, max_slots=4, keep_final=True,
-                     seed=SEED, msgs_per_step=(20, 60), window_buckets=buckets)
+                     seed=SEED, msgs_per_step=(20, 60), window_buckets=buckets,
+                     independent=bool(buckets))
         rep = srv.run(_clone(eps), clock="virtual")
         assert rep["episode_steps"] == sum(e.n_steps for e in eps)
         assert len(srv.pools) == len(CAPS) * (len(buckets) + 1)
