@@ -395,6 +395,8 @@ def run_engine(args):
     if rank == 0 and args.oracle_books > 0:
         cpu, parity = cpu_baseline_and_parity(e, msgs, off, counts, cap, tcap, depth,
                                               args.oracle_books, w)
+        if world > 1:  # the CPU baseline is reported at N = 1 only; parity at every N
+            cpu = None
 
     # ---------------- roofline of the processing kernel
     peak, peak_kind = measured_peaks()
@@ -417,7 +419,9 @@ def run_engine(args):
                                    else "no counter record for these kernel sources")
 
     extras = None
-    if not args.no_extras and args.workload == "replay_1024x100k":
+    # the other workloads are single-GPU legs: a run on N > 1 GPUs measures the
+    # headline's scaling only and holds the GPUs no longer than that needs
+    if not args.no_extras and args.workload == "replay_1024x100k" and world == 1:
         e.close()
         del d_msgs
         torch.cuda.empty_cache()
